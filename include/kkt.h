@@ -1,0 +1,220 @@
+/*
+ * kkt.h -- C interface of the fixed-pattern KKT refactorization library.
+ *
+ * The library factors a sequence of sparse matrices that share one sparsity
+ * pattern while their values change at every interior-point iteration
+ * (arXiv 2306.14337, Sec. 2, Eq. 4 and the remark after it: all K_k have the
+ * same pattern, so work on the pattern should be reused).  It follows the
+ * paper's three phases (Sec. 4): a host-side analysis once per pattern, then
+ * for every value set a numeric refactorization with the same pivot sequence
+ * (Sec. 4 "refactorization", Sec. 5), triangular solves, and iterative
+ * refinement (Sec. 5.1).  Everything after the analysis runs in this
+ * library's CUDA kernels on one GPU; the host only launches them.
+ *
+ * Conventions shared by all calls
+ *   - Indices are int32, values float64.  The matrix is given in compressed
+ *     sparse row form (row_ptr[n+1], col_idx[nnz]) with strictly increasing
+ *     column indices in every row; values are in the same order.
+ *   - "_dev" pointers are device pointers on the context's device; the
+ *     caller owns them, keeps them valid until the stream reaches the call,
+ *     and may reuse them afterwards.  "_host" pointers are host memory.
+ *   - The context owns the factors and every workspace buffer; all of it is
+ *     allocated by kkt_analyze (Sec. 5.1: buffers allocated once and reused).
+ *   - Calls that take a stream are asynchronous on that stream (NULL = the
+ *     legacy default stream) unless stated otherwise.  Conditions found on
+ *     the device (perturbed pivots, non-finite values, a wait that ran out)
+ *     accumulate in a device status word read by kkt_status_sync.  Errors
+ *     found on the host return at once and launch nothing.
+ *   - Calls on one context must be ordered on one stream; a context is not
+ *     safe for concurrent use from several host threads.
+ */
+#ifndef KKT_H
+#define KKT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kkt_ctx kkt_ctx;
+typedef void *kkt_stream; /* a cudaStream_t */
+
+typedef enum {
+    KKT_OK = 0,
+    KKT_ERR_ARG = 1,            /* invalid argument (null pointer, size, option) */
+    KKT_ERR_PATTERN = 2,        /* unsorted / duplicate / out-of-range index, n <= 0 */
+    KKT_ERR_ALLOC = 3,          /* host or device allocation failed */
+    KKT_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    KKT_ERR_NONFINITE = 5,      /* a value or a computed pivot was NaN or infinite */
+    KKT_ERR_NOT_CONVERGED = 6,  /* refinement did not reach tol in max_it solves;
+                                   the caller may re-analyze (Sec. 5.1) */
+    KKT_ERR_TIMEOUT = 7,        /* a bounded device wait ran out; results invalid */
+    KKT_ERR_STATE = 8,          /* call out of order (e.g. solve before refactor),
+                                   or a device call on a host-only context */
+    KKT_ERR_INTERNAL = 9,       /* a device-side consistency check failed */
+    KKT_WARN_PERTURBED = 100    /* success, but some pivots were perturbed */
+} kkt_status;
+
+enum { KKT_ORDER_AMD = 0, KKT_ORDER_NATURAL = 1, KKT_ORDER_USER = 2 };
+enum { KKT_REFINE_CLASSIC = 0, KKT_REFINE_FGMRES = 1, KKT_REFINE_AUTO = 2 };
+
+typedef struct {
+    int factor_fp32;        /* 0: factors and triangular solves in FP64;
+                               1: in FP32 (residual, update, pivot test stay FP64) */
+    int equilibrate;        /* 1: power-of-two symmetric scaling s_i = 2^-floor(floor(log2 r_i)/2),
+                               r_i = max_j |a_ij|, recomputed at every refactorization */
+    int ordering;           /* KKT_ORDER_*: approximate minimum degree on A + A^T
+                               (Sec. 5.2), identity, or user_perm */
+    const int *user_perm;   /* ordering == USER: host array, perm[new] = old, length n;
+                               copied during kkt_analyze */
+    int refine_mode;        /* KKT_REFINE_*: classic (Sec. 5.1 x += K^-1 (r - K x)),
+                               FGMRES with the LU solve as right preconditioner and
+                               CGS2 (Sec. 5.1), or classic switching to FGMRES when an
+                               iteration fails to halve the scaled residual */
+    int fgmres_restart;     /* Krylov basis size (default 20) */
+    int max_refine;         /* default limit on solves in kkt_refine (20, Sec. 5.3) */
+    double tol;             /* default scaled-residual target (1e-14, Sec. 5.3) */
+    double pivot_tau_rel;   /* perturbation threshold relative to max|A'|; 0 selects
+                               1e-14 (FP64 factors) or 2^-24 (FP32 factors) */
+    long long spin_limit;   /* polls before a device wait gives up (KKT_ERR_TIMEOUT) */
+    int device;             /* CUDA device ordinal; -1 = host-only analysis (no CUDA
+                               call at all; only the kkt_get_* / export calls work) */
+    int max_batch;          /* capacity of the batched calls, fixed at analysis */
+    int cta_warps;          /* warps per CTA of the persistent kernels (1..8; 0 = 8) */
+    int refactor_ctas;      /* CTAs of the refactorization (0 = all that fit at once) */
+    int solve_ctas;         /* CTAs of the triangular solves (0 = 2 per SM) */
+} kkt_options;
+
+typedef struct {
+    int n;                  /* dimension */
+    long long nnz_a;        /* stored entries of the user pattern */
+    long long nnz_sym;      /* entries of A + A^T + I */
+    long long nnz_lu;       /* entries of combined L+U (diagonal once) */
+    int n_levels;           /* levels of the refactorization / forward solve */
+    int n_levels_u;         /* levels of the backward solve */
+    int max_row;            /* longest row of L+U */
+    double flops_refactor;  /* sum over pivots d of |L(:,d)| (1 + 2 |U(d,:)|) */
+    double bytes_refactor;  /* compulsory bytes of one refactorization */
+    double bytes_solve;     /* compulsory bytes of one forward + backward solve */
+    double bytes_spmv;      /* compulsory bytes of one residual */
+    size_t device_bytes;    /* device memory held by the context */
+    int grid_ctas;          /* CTAs of the refactorization */
+    int solve_ctas;         /* CTAs of the triangular solves */
+    int warps_per_cta;
+    int last_refine_iters;  /* solves used by the last kkt_refine */
+    double last_omega;      /* scaled residual after the last kkt_refine */
+    int factor_fp32;
+    long long kernel_launches; /* CUDA kernels this context has launched so far */
+} kkt_stats;
+
+typedef struct {
+    int iters;              /* solves with the factors used */
+    int converged;          /* 1 if omega <= tol */
+    double omega;           /* final scaled residual */
+    double omega_hist[64];  /* omega before each solve and after the last (first 64) */
+    int n_hist;
+} kkt_refine_info;
+
+/* Fill *opt with the defaults listed above (AMD, equilibration on, FP64). */
+void kkt_default_options(kkt_options *opt);
+
+/* Human-readable name of a status code (static storage). */
+const char *kkt_status_string(kkt_status s);
+
+/* Text of the last host-detected error on the calling thread ("" if none);
+ * valid until the next call on that thread. */
+const char *kkt_last_error(void);
+
+/*
+ * Analyze a pattern once (Sec. 4 symbolic phase; Sec. 5.2 preprocessing:
+ * symmetric fill-reducing ordering of A + A^T, symbolic LU, reused for every
+ * later value set).  Host only; then copies the index structures to the device
+ * once (Sec. 5: data moves to the GPU once) and allocates all workspace.
+ *   n, row_ptr[n+1], col_idx[nnz]: host CSR, sorted and unique per row.
+ *   opt: NULL for defaults.
+ *   out: receives the new context (NULL on failure).
+ * Missing diagonal entries are added as structural zeros.  Errors:
+ * KKT_ERR_PATTERN for a malformed pattern, KKT_ERR_ARG for a bad option or
+ * user permutation, KKT_ERR_ALLOC / KKT_ERR_CUDA.
+ */
+kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx,
+                       const kkt_options *opt, kkt_ctx **out);
+
+/* Release everything the context holds.  NULL is allowed. */
+void kkt_destroy(kkt_ctx *ctx);
+
+/*
+ * Numeric refactorization with the fixed pivot sequence (Sec. 4
+ * refactorization; Sec. 5.2: fill A's values into the combined L+U storage,
+ * then factor).  values_dev: nnz float64 in the CSR order given to analyze.
+ * The context keeps the pointer: residuals of later kkt_refine calls read the
+ * original matrix from it, so it must stay valid and unchanged until the next
+ * kkt_refactor.  Perturbed pivots (|p| below tau, Sec. 5 static-pivot
+ * reading) are counted in the device status word.
+ */
+kkt_status kkt_refactor(kkt_ctx *ctx, const double *values_dev, kkt_stream stream);
+
+/* x = A^-1 b with the current factors (permute/scale fused, Sec. 5.2).
+ * b_dev, x_dev: n float64; they may not alias. */
+kkt_status kkt_solve(kkt_ctx *ctx, const double *b_dev, double *x_dev, kkt_stream stream);
+
+/* lam = A^-T g with the same factors (A'^T = U^T L^T).  g_dev, lam_dev: n float64. */
+kkt_status kkt_solve_transpose(kkt_ctx *ctx, const double *g_dev, double *lam_dev,
+                               kkt_stream stream);
+
+/*
+ * Iterative refinement (Sec. 5.1) of x_dev (in/out, n float64) for A x = b
+ * until omega = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) <= tol or
+ * max_it solves were used (tol <= 0 / max_it < 0 select the context's
+ * defaults).  The residual is FP64 on the original A.  Reads omega on the host
+ * once per iteration, so this call synchronizes the stream.  info (host, may
+ * be NULL) receives the history.  Returns KKT_ERR_NOT_CONVERGED when the
+ * target was missed.
+ */
+kkt_status kkt_refine(kkt_ctx *ctx, const double *b_dev, double *x_dev, double tol,
+                      int max_it, kkt_refine_info *info, kkt_stream stream);
+
+/* Same for the transposed system A^T lam = g. */
+kkt_status kkt_refine_transpose(kkt_ctx *ctx, const double *g_dev, double *lam_dev,
+                                double tol, int max_it, kkt_refine_info *info,
+                                kkt_stream stream);
+
+/*
+ * Gradient of x = A^-1 b: dA_k = -lam[row_k] * x[col_k] for every stored
+ * entry k of the user pattern (nnz float64, CSR order); the gradient of b is
+ * lam itself.  lam_dev, x_dev: n float64.
+ */
+kkt_status kkt_adjoint_gather(kkt_ctx *ctx, const double *lam_dev, const double *x_dev,
+                              double *dA_dev, kkt_stream stream);
+
+/* Synchronize the stream, read and clear the device status word.  Returns
+ * KKT_ERR_INTERNAL, KKT_ERR_TIMEOUT, KKT_ERR_NONFINITE, KKT_WARN_PERTURBED or KKT_OK;
+ * *n_perturbed (may be NULL) receives the count of perturbed pivots. */
+kkt_status kkt_status_sync(kkt_ctx *ctx, kkt_stream stream, int *n_perturbed);
+
+/* Sizes, byte and flop counts of the analysis (host, no synchronization). */
+kkt_status kkt_get_stats(const kkt_ctx *ctx, kkt_stats *stats);
+
+/*
+ * Copy the analysis to host arrays (sizes from kkt_get_stats):
+ *   perm[n] (new -> old), lu_row_ptr[n+1], lu_col_idx[nnz_lu] (pattern of
+ *   combined L+U of the permuted matrix, row-wise, sorted),
+ *   level[n], level_u[n] (forward and backward level of every permuted row).
+ * Any pointer may be NULL to skip that array.
+ */
+kkt_status kkt_export_symbolic(const kkt_ctx *ctx, int *perm, int *lu_row_ptr,
+                               int *lu_col_idx, int *level, int *level_u);
+
+/* Copy the current factor values (float64, in lu_col_idx order; L strictly
+ * below the diagonal, U on and above it) to out_dev (nnz_lu float64). */
+kkt_status kkt_export_factors(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
+
+/* Copy the current scaling s (n float64, original indexing) to out_dev. */
+kkt_status kkt_export_scaling(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KKT_H */

@@ -210,6 +210,21 @@ class Factor:
     def U_csc(self):
         return sp.csc_matrix((self.Ux, self.Ui, self.Up), shape=(self.n, self.n))
 
+    def lu_csr(self):
+        """Combined L+U row by row: (row_ptr, col_idx, values, error bounds),
+        L strictly below the diagonal, U on and above it, columns ascending."""
+        n = self.n
+        lcol = np.repeat(np.arange(n), np.diff(self.Lp))
+        ucol = np.repeat(np.arange(n), np.diff(self.Up))
+        rows = np.concatenate([self.Li, self.Ui]).astype(np.int64)
+        cols = np.concatenate([lcol, ucol]).astype(np.int64)
+        vals = np.concatenate([self.Lx, self.Ux])
+        errs = np.concatenate([self.Le, self.Ue])
+        order = np.argsort(rows * n + cols, kind="stable")
+        rp = np.zeros(n + 1, dtype=np.int64)
+        np.add.at(rp, rows + 1, 1)
+        return _i32(np.cumsum(rp)), _i32(cols[order]), vals[order], errs[order]
+
     def lu_pattern_csr(self):
         """Combined L+U pattern as CSR (row-wise), the layout used for
         comparisons with the library's analysis."""

@@ -1,0 +1,396 @@
+// analysis.cpp -- host-side analysis of a fixed sparsity pattern.
+//
+// arXiv 2306.14337: the symbolic phase runs once on the host (Sec. 4); the
+// matrix is reordered with a symmetric fill-reducing ordering of A + A^T
+// (Sec. 5.2) and the pattern of the combined L+U storage is computed once and
+// reused by every later refactorization (Sec. 5.2, "symbolic factorization").
+//
+// This file uses its own algorithms: an approximate-minimum-degree ordering on
+// a quotient graph (elements, supervariables, approximate external degrees,
+// element absorption), the elimination tree by path compression, and the row
+// patterns of L as row subtrees of that tree.  Levels are elimination-tree
+// heights (forward) and depths (backward).
+#include "analysis.h"
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+namespace kkt {
+
+int validate_pattern(int n, const int *rp, const int *ci) {
+    if (n <= 0 || !rp || !ci) return A_ERR_PATTERN;
+    if (rp[0] != 0) return A_ERR_PATTERN;
+    for (int i = 0; i < n; i++) {
+        if (rp[i + 1] < rp[i]) return A_ERR_PATTERN;
+        for (int p = rp[i]; p < rp[i + 1]; p++) {
+            if (ci[p] < 0 || ci[p] >= n) return A_ERR_PATTERN;
+            if (p > rp[i] && ci[p] <= ci[p - 1]) return A_ERR_PATTERN;
+        }
+    }
+    return A_OK;
+}
+
+void symmetric_graph(int n, const int *rp, const int *ci, std::vector<int> &grp,
+                     std::vector<int> &gci) {
+    std::vector<int> cnt(n + 1, 0);
+    for (int i = 0; i < n; i++)
+        for (int p = rp[i]; p < rp[i + 1]; p++)
+            if (ci[p] != i) { cnt[i + 1]++; cnt[ci[p] + 1]++; }
+    for (int i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+    std::vector<int> tmp(cnt[n]);
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int i = 0; i < n; i++)
+        for (int p = rp[i]; p < rp[i + 1]; p++)
+            if (ci[p] != i) { tmp[fill[i]++] = ci[p]; tmp[fill[ci[p]]++] = i; }
+    grp.assign(n + 1, 0);
+    gci.clear();
+    gci.reserve(tmp.size());
+    for (int i = 0; i < n; i++) {
+        auto b = tmp.begin() + cnt[i], e = tmp.begin() + cnt[i + 1];
+        std::sort(b, e);
+        auto u = std::unique(b, e);
+        gci.insert(gci.end(), b, u);
+        grp[i + 1] = (int)gci.size();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Approximate minimum degree.
+//
+// Quotient graph: every index is either a variable (not yet eliminated) or an
+// element (an eliminated pivot, standing for the clique it created).  A
+// variable i keeps the variables it is still directly adjacent to (A[i]) and
+// the elements it belongs to (E[i]); an element e keeps its variables (Le[e]).
+// Eliminating pivot p turns it into an element whose variable set is the union
+// of A[p] and of the sets of the elements around p, which are absorbed.  The
+// external degree of each affected variable is bounded from above by
+//   |A_i| + |L_p \ i| + sum_{e in E_i, e != p} |L_e \ L_p|
+// (weighted by supervariable size), the approximation of Amestoy, Davis and
+// Duff (1996); |L_e \ L_p| is obtained by subtracting from |L_e| the weights
+// of the variables of L_p that lie in e.  Elements with |L_e \ L_p| = 0 are
+// absorbed into p.  Variables of L_p with identical adjacency are merged into
+// supervariables and eliminated together.
+void amd_order(int n, const std::vector<int> &grp, const std::vector<int> &gci,
+               std::vector<int> &perm) {
+    enum : char { VAR = 0, ELEM = 1, DEAD = 2, MERGED = 3 };
+    std::vector<std::vector<int>> A(n), E(n), Le(n);
+    std::vector<int> nv(n, 1), deg(n, 0), rep(n, -1);
+    std::vector<long long> wsz(n, 0), w(n, 0);
+    std::vector<char> st(n, VAR);
+    std::vector<int> head(n + 1, -1), nxt(n, -1), prv(n, -1);
+    std::vector<int> mark(n, 0), wtag(n, 0);
+    int tag = 0;
+
+    auto bucket_insert = [&](int i, int d) {
+        deg[i] = d;
+        nxt[i] = head[d];
+        prv[i] = -1;
+        if (head[d] >= 0) prv[head[d]] = i;
+        head[d] = i;
+    };
+    auto bucket_remove = [&](int i) {
+        int d = deg[i];
+        if (prv[i] >= 0) nxt[prv[i]] = nxt[i]; else head[d] = nxt[i];
+        if (nxt[i] >= 0) prv[nxt[i]] = prv[i];
+        nxt[i] = prv[i] = -1;
+    };
+    for (int i = 0; i < n; i++) {
+        A[i].assign(gci.begin() + grp[i], gci.begin() + grp[i + 1]);
+        bucket_insert(i, std::min((int)A[i].size(), n));
+    }
+    std::vector<int> elim;
+    elim.reserve(n);
+    std::vector<int> Lp, nd(n, 0);
+    int mindeg = 0;
+    long long k = 0;
+    while (k < n) {
+        while (mindeg <= n && head[mindeg] < 0) mindeg++;
+        if (mindeg > n) break;  // cannot happen: weights sum to n
+        int p = head[mindeg];
+        bucket_remove(p);
+        elim.push_back(p);
+        k += nv[p];
+        ++tag;
+        // variables of the new element
+        Lp.clear();
+        mark[p] = tag;
+        for (int e : E[p]) {
+            if (st[e] != ELEM) continue;
+            for (int i : Le[e])
+                if (st[i] == VAR && mark[i] != tag) { mark[i] = tag; Lp.push_back(i); }
+            st[e] = DEAD;
+            std::vector<int>().swap(Le[e]);
+        }
+        for (int i : A[p])
+            if (st[i] == VAR && mark[i] != tag) { mark[i] = tag; Lp.push_back(i); }
+        st[p] = ELEM;
+        std::vector<int>().swap(A[p]);
+        std::vector<int>().swap(E[p]);
+        long long lpw = 0;
+        for (int i : Lp) { lpw += nv[i]; bucket_remove(i); }
+        // |L_e \ L_p| for every element touching L_p
+        for (int i : Lp)
+            for (int e : E[i]) {
+                if (st[e] != ELEM) continue;
+                if (wtag[e] != tag) { wtag[e] = tag; w[e] = wsz[e]; }
+                w[e] -= nv[i];
+            }
+        // prune adjacency, absorb covered elements, bound the degree
+        for (int i : Lp) {
+            std::vector<int> ne;
+            ne.reserve(E[i].size() + 1);
+            long long de = 0;
+            for (int e : E[i]) {
+                if (st[e] != ELEM) continue;
+                if (w[e] == 0) { st[e] = DEAD; std::vector<int>().swap(Le[e]); continue; }
+                ne.push_back(e);
+                de += w[e];
+            }
+            ne.push_back(p);
+            std::sort(ne.begin(), ne.end());
+            std::vector<int> na;
+            na.reserve(A[i].size());
+            long long da = 0;
+            for (int j : A[i])
+                if (st[j] == VAR && mark[j] != tag) { na.push_back(j); da += nv[j]; }
+            std::sort(na.begin(), na.end());
+            A[i].swap(na);
+            E[i].swap(ne);
+            long long rest = (long long)n - k - nv[i];
+            long long d = da + de + (lpw - nv[i]);
+            d = std::min(d, (long long)deg[i] + lpw - nv[i]);
+            d = std::min(d, rest);
+            nd[i] = (int)std::max(0LL, d);
+        }
+        // supervariables: identical A and E among the variables of L_p
+        if (Lp.size() > 1) {
+            std::vector<std::pair<unsigned long long, int>> key;
+            key.reserve(Lp.size());
+            for (int i : Lp) {
+                unsigned long long h = 1469598103934665603ULL;
+                for (int j : A[i]) h = (h ^ (unsigned)j) * 1099511628211ULL;
+                h = (h ^ 0x9e3779b9ULL) * 1099511628211ULL;
+                for (int e : E[i]) h = (h ^ (unsigned)e) * 1099511628211ULL;
+                key.push_back({h, i});
+            }
+            std::sort(key.begin(), key.end());
+            for (size_t a = 0; a < key.size();) {
+                size_t b = a;
+                while (b < key.size() && key[b].first == key[a].first) b++;
+                for (size_t x = a; x < b; x++) {
+                    int i = key[x].second;
+                    if (st[i] != VAR) continue;
+                    for (size_t y = x + 1; y < b; y++) {
+                        int j = key[y].second;
+                        if (st[j] != VAR) continue;
+                        if (A[i] == A[j] && E[i] == E[j]) {
+                            nv[i] += nv[j];
+                            nd[i] -= nv[j];
+                            nv[j] = 0;
+                            st[j] = MERGED;
+                            rep[j] = i;
+                            std::vector<int>().swap(A[j]);
+                            std::vector<int>().swap(E[j]);
+                        }
+                    }
+                }
+                a = b;
+            }
+        }
+        Le[p] = Lp;
+        wsz[p] = lpw;
+        for (int i : Lp) {
+            if (st[i] != VAR) continue;
+            int d = std::min(std::max(nd[i], 0), n);
+            bucket_insert(i, d);
+            if (d < mindeg) mindeg = d;
+        }
+    }
+    // pivots in elimination order, each followed by the variables merged into it
+    std::vector<std::vector<int>> kids(n);
+    for (int j = 0; j < n; j++)
+        if (rep[j] >= 0) kids[rep[j]].push_back(j);
+    perm.clear();
+    perm.reserve(n);
+    std::vector<int> stack;
+    for (int p : elim) {
+        stack.assign(1, p);
+        while (!stack.empty()) {
+            int v = stack.back();
+            stack.pop_back();
+            perm.push_back(v);
+            for (auto it = kids[v].rbegin(); it != kids[v].rend(); ++it) stack.push_back(*it);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+static int find_slot(const std::vector<int> &rp, const std::vector<int> &ci, int row, int col) {
+    auto b = ci.begin() + rp[row], e = ci.begin() + rp[row + 1];
+    auto it = std::lower_bound(b, e, col);
+    if (it == e || *it != col) return -1;
+    return (int)(it - ci.begin());
+}
+
+int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
+            Analysis &out, std::string &err) {
+    int rc = validate_pattern(n, rp, ci);
+    if (rc) { err = "malformed CSR pattern (n <= 0, unsorted, duplicate or out-of-range index)"; return rc; }
+    if (rp[n] > (1 << 30)) { err = "too many entries"; return A_ERR_ARG; }
+    Analysis &a = out;
+    a.n = n;
+    a.a_rp.assign(rp, rp + n + 1);
+    a.a_ci.assign(ci, ci + rp[n]);
+    a.a_row.resize(rp[n]);
+    for (int i = 0; i < n; i++)
+        for (int p = rp[i]; p < rp[i + 1]; p++) a.a_row[p] = i;
+
+    std::vector<int> grp, gci;
+    symmetric_graph(n, rp, ci, grp, gci);
+    a.nnz_sym = (long long)gci.size() + n;
+
+    // ordering
+    if (ordering == 0) {
+        amd_order(n, grp, gci, a.perm);
+    } else if (ordering == 1) {
+        a.perm.resize(n);
+        std::iota(a.perm.begin(), a.perm.end(), 0);
+    } else if (ordering == 2) {
+        if (!user_perm) { err = "user ordering requested without user_perm"; return A_ERR_ARG; }
+        a.perm.assign(user_perm, user_perm + n);
+    } else {
+        err = "unknown ordering";
+        return A_ERR_ARG;
+    }
+    if ((int)a.perm.size() != n) { err = "ordering has wrong length"; return A_ERR_ARG; }
+    a.iperm.assign(n, -1);
+    for (int i = 0; i < n; i++) {
+        int o = a.perm[i];
+        if (o < 0 || o >= n || a.iperm[o] >= 0) { err = "ordering is not a permutation"; return A_ERR_ARG; }
+        a.iperm[o] = i;
+    }
+
+    // permuted symmetric graph: neighbours of new vertex i, sorted
+    std::vector<int> prp(n + 1, 0), pci(gci.size());
+    for (int i = 0; i < n; i++) prp[i + 1] = prp[i] + (grp[a.perm[i] + 1] - grp[a.perm[i]]);
+    for (int i = 0; i < n; i++) {
+        int o = a.perm[i], q = prp[i];
+        for (int p = grp[o]; p < grp[o + 1]; p++) pci[q++] = a.iperm[gci[p]];
+        std::sort(pci.begin() + prp[i], pci.begin() + prp[i + 1]);
+    }
+
+    // elimination tree by path compression over virtual ancestors
+    a.parent.assign(n, -1);
+    std::vector<int> anc(n, -1);
+    for (int i = 0; i < n; i++) {
+        for (int p = prp[i]; p < prp[i + 1]; p++) {
+            int r = pci[p];
+            if (r >= i) break;
+            while (anc[r] != -1 && anc[r] != i) {
+                int t = anc[r];
+                anc[r] = i;
+                r = t;
+            }
+            if (anc[r] == -1) { anc[r] = i; a.parent[r] = i; }
+        }
+    }
+
+    // row patterns of L: row subtree of i = union of tree paths from each
+    // j < i adjacent to i up to i
+    std::vector<int> lrp(n + 1, 0);
+    std::vector<int> lci;
+    lci.reserve(gci.size() * 3);
+    std::vector<int> mk(n, -1);
+    for (int i = 0; i < n; i++) {
+        size_t start = lci.size();
+        mk[i] = i;
+        for (int p = prp[i]; p < prp[i + 1]; p++) {
+            int r = pci[p];
+            if (r >= i) break;
+            while (r >= 0 && mk[r] != i) {
+                mk[r] = i;
+                lci.push_back(r);
+                r = a.parent[r];
+            }
+            if (r < 0) { err = "internal: elimination tree path does not reach its row"; return A_ERR_ARG; }
+        }
+        std::sort(lci.begin() + start, lci.end());
+        lrp[i + 1] = (int)lci.size();
+    }
+    // rows of U = columns of L (pattern symmetric)
+    std::vector<int> ucnt(n + 1, 0);
+    for (size_t q = 0; q < lci.size(); q++) ucnt[lci[q] + 1]++;
+    for (int i = 0; i < n; i++) ucnt[i + 1] += ucnt[i];
+    std::vector<int> uci(lci.size()), ufill(ucnt.begin(), ucnt.end() - 1);
+    for (int i = 0; i < n; i++)
+        for (int p = lrp[i]; p < lrp[i + 1]; p++) uci[ufill[lci[p]]++] = i;  // ascending i
+    // combined rows
+    long long nnz = (long long)lci.size() * 2 + n;
+    if (nnz > (1LL << 31) - 1) { err = "factor too large for 32-bit indices"; return A_ERR_ARG; }
+    a.lu_rp.assign(n + 1, 0);
+    a.lu_ci.resize(nnz);
+    a.diag.resize(n);
+    {
+        long long q = 0;
+        for (int i = 0; i < n; i++) {
+            for (int p = lrp[i]; p < lrp[i + 1]; p++) a.lu_ci[q++] = lci[p];
+            a.diag[i] = (int)q;
+            a.lu_ci[q++] = i;
+            for (int p = ucnt[i]; p < ucnt[i + 1]; p++) a.lu_ci[q++] = uci[p];
+            a.lu_rp[i + 1] = (int)q;
+        }
+    }
+    a.max_row = 0;
+    for (int i = 0; i < n; i++) a.max_row = std::max(a.max_row, a.lu_rp[i + 1] - a.lu_rp[i]);
+
+    // user entry -> slot
+    a.src.assign(nnz, -1);
+    for (int r = 0; r < n; r++)
+        for (int p = rp[r]; p < rp[r + 1]; p++) {
+            int s = find_slot(a.lu_rp, a.lu_ci, a.iperm[r], a.iperm[ci[p]]);
+            if (s < 0) { err = "internal: user entry outside the filled pattern"; return A_ERR_ARG; }
+            a.src[s] = p;
+        }
+    // transposed slots
+    a.tpos.resize(nnz);
+    for (int i = 0; i < n; i++)
+        for (int p = a.lu_rp[i]; p < a.lu_rp[i + 1]; p++) {
+            int j = a.lu_ci[p];
+            int s = (j == i) ? p : find_slot(a.lu_rp, a.lu_ci, j, i);
+            if (s < 0) { err = "internal: pattern not symmetric"; return A_ERR_ARG; }
+            a.tpos[p] = s;
+        }
+
+    // levels: height (leaves 0) and depth (roots 0) in the elimination tree
+    a.level.assign(n, 0);
+    for (int i = 0; i < n; i++)
+        if (a.parent[i] >= 0) a.level[a.parent[i]] = std::max(a.level[a.parent[i]], a.level[i] + 1);
+    a.level_u.assign(n, 0);
+    for (int i = n - 1; i >= 0; i--)
+        if (a.parent[i] >= 0) a.level_u[i] = a.level_u[a.parent[i]] + 1;
+    a.n_levels = *std::max_element(a.level.begin(), a.level.end()) + 1;
+    a.n_levels_u = *std::max_element(a.level_u.begin(), a.level_u.end()) + 1;
+    auto by_level = [n](const std::vector<int> &lev, int nl, std::vector<int> &ord) {
+        std::vector<int> c(nl + 1, 0);
+        for (int i = 0; i < n; i++) c[lev[i] + 1]++;
+        for (int l = 0; l < nl; l++) c[l + 1] += c[l];
+        ord.resize(n);
+        for (int i = 0; i < n; i++) ord[c[lev[i]]++] = i;
+    };
+    by_level(a.level, a.n_levels, a.order_f);
+    by_level(a.level_u, a.n_levels_u, a.order_b);
+
+    // flops of one refactorization: each pivot d eliminated from the rows of
+    // L(:,d) costs one division and a multiply-add per entry of U(d, >d)
+    double fl = 0.0;
+    for (int d = 0; d < n; d++) {
+        double lcol = ucnt[d + 1] - ucnt[d];       // |L(:,d)| = |U(d,:)| off-diagonal
+        fl += lcol * (1.0 + 2.0 * lcol);
+    }
+    a.flops = fl;
+    return A_OK;
+}
+
+}  // namespace kkt

@@ -1,0 +1,56 @@
+// analysis.h -- host-side pattern analysis (one per sparsity pattern).
+//
+// Produces everything the device kernels need to refactor and solve a matrix
+// of a fixed pattern (arXiv 2306.14337, Sec. 4 symbolic phase, Sec. 5.2
+// preprocessing): a symmetric fill-reducing permutation, the pattern of the
+// combined L+U factor stored row by row, the dependency levels, and the maps
+// that place user values and transposed entries.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace kkt {
+
+struct Analysis {
+    int n = 0;
+    // user pattern (copied)
+    std::vector<int> a_rp, a_ci;
+    std::vector<int> a_row;        // row of every user entry
+    // ordering: perm[new] = old, iperm[old] = new
+    std::vector<int> perm, iperm;
+    // elimination tree of the permuted symmetric pattern
+    std::vector<int> parent;
+    // combined L+U pattern of the permuted matrix, CSR, columns ascending
+    std::vector<int> lu_rp, lu_ci;
+    std::vector<int> diag;         // position of the diagonal in each row
+    std::vector<int> src;          // user entry stored in each slot, or -1
+    std::vector<int> tpos;         // slot of the transposed entry (diagonal: itself)
+    // levels and schedules
+    std::vector<int> level, level_u;
+    std::vector<int> order_f;      // rows by (level, index)
+    std::vector<int> order_b;      // rows by (level_u, index)
+    int n_levels = 0, n_levels_u = 0;
+    long long nnz_sym = 0;
+    int max_row = 0;
+    double flops = 0.0;
+};
+
+// Status codes match kkt_status.
+enum { A_OK = 0, A_ERR_ARG = 1, A_ERR_PATTERN = 2, A_ERR_ALLOC = 3 };
+
+int validate_pattern(int n, const int *rp, const int *ci);
+
+// Adjacency of A + A^T without the diagonal (CSR, sorted, unique).
+void symmetric_graph(int n, const int *rp, const int *ci, std::vector<int> &grp,
+                     std::vector<int> &gci);
+
+// Approximate minimum degree ordering of a symmetric graph (no self loops).
+void amd_order(int n, const std::vector<int> &grp, const std::vector<int> &gci,
+               std::vector<int> &perm);
+
+// Full analysis.  ordering: 0 AMD, 1 natural, 2 user (user_perm, new -> old).
+int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
+            Analysis &out, std::string &err);
+
+}  // namespace kkt

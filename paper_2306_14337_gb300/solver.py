@@ -1,0 +1,210 @@
+"""Torch-facing wrapper of the C interface: device memory and streams come
+from PyTorch, all arithmetic runs in ``libkkt.so``.
+
+``KKTSolver`` mirrors the C calls one to one; ``kkt_solve`` is the
+differentiable solve (forward: refactor + solve + refine; backward: the
+transposed solve with the same factors, then the adjoint gather kernel).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _capi
+from ._capi import check
+
+_ORDER = {"amd": _capi.ORDER_AMD, "natural": _capi.ORDER_NATURAL, "user": _capi.ORDER_USER}
+_REFINE = {"classic": _capi.REFINE_CLASSIC, "fgmres": _capi.REFINE_FGMRES, "auto": _capi.REFINE_AUTO}
+
+
+def _ptr(t: torch.Tensor):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+class KKTSolver:
+    """One analysed sparsity pattern and its device-resident factors.
+
+    indptr, indices: CSR pattern (host arrays, sorted and unique per row).
+    device: CUDA device index, or None for a host-only analysis (no CUDA call;
+    only ``stats`` and ``export_symbolic`` work).
+    """
+
+    def __init__(self, n, indptr, indices, *, fp32=False, equilibrate=True, ordering="amd",
+                 perm=None, refine_mode="classic", tol=1e-14, max_refine=20,
+                 pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
+                 solve_ctas=0, device=0):
+        self._lib = _capi.load()
+        self.n = int(n)
+        self._rp = _i32(indptr)
+        self._ci = _i32(indices)
+        self.nnz = int(self._ci.size)
+        opt = _capi.Options()
+        self._lib.kkt_default_options(C.byref(opt))
+        opt.factor_fp32 = int(bool(fp32))
+        opt.equilibrate = int(bool(equilibrate))
+        opt.ordering = _ORDER["user" if perm is not None else ordering]
+        self._perm = None
+        if perm is not None:
+            self._perm = _i32(perm)
+            opt.user_perm = self._perm.ctypes.data_as(C.POINTER(C.c_int))
+        opt.refine_mode = _REFINE[refine_mode]
+        opt.tol = float(tol)
+        opt.max_refine = int(max_refine)
+        opt.pivot_tau_rel = float(pivot_tau_rel)
+        opt.spin_limit = int(spin_limit)
+        opt.cta_warps = int(cta_warps)
+        opt.refactor_ctas = int(refactor_ctas)
+        opt.solve_ctas = int(solve_ctas)
+        self.device = None if device is None else torch.device("cuda", int(device)) if not isinstance(
+            device, torch.device) else device
+        opt.device = -1 if self.device is None else (self.device.index or 0)
+        self.fp32 = bool(fp32)
+        h = C.c_void_p()
+        st = self._lib.kkt_analyze(self.n, self._rp.ctypes.data_as(C.POINTER(C.c_int)),
+                                   self._ci.ctypes.data_as(C.POINTER(C.c_int)), C.byref(opt),
+                                   C.byref(h))
+        check(st, "kkt_analyze")
+        self._h = h
+        self._values = None
+        self.version = 0           # bumped by every refactor
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.kkt_destroy(h)
+            self._h = None
+
+    # ----------------------------------------------------------------- info
+    def stats(self) -> dict:
+        s = _capi.Stats()
+        check(self._lib.kkt_get_stats(self._h, C.byref(s)), "kkt_get_stats")
+        return {name: getattr(s, name) for name, _ in _capi.Stats._fields_}
+
+    def export_symbolic(self):
+        st = self.stats()
+        n, m = st["n"], st["nnz_lu"]
+        perm = np.zeros(n, np.int32)
+        rp = np.zeros(n + 1, np.int32)
+        ci = np.zeros(m, np.int32)
+        lev = np.zeros(n, np.int32)
+        levu = np.zeros(n, np.int32)
+        P = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+        check(self._lib.kkt_export_symbolic(self._h, P(perm), P(rp), P(ci), P(lev), P(levu)),
+              "kkt_export_symbolic")
+        return dict(perm=perm, lu_rp=rp, lu_ci=ci, level=lev, level_u=levu)
+
+    def export_factors(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.stats()["nnz_lu"], dtype=torch.float64, device=self.device)
+        check(self._lib.kkt_export_factors(self._h, _ptr(out), _stream(stream)), "kkt_export_factors")
+        return out
+
+    def export_scaling(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        check(self._lib.kkt_export_scaling(self._h, _ptr(out), _stream(stream)), "kkt_export_scaling")
+        return out
+
+    def status(self, stream=None):
+        """(status code, perturbed-pivot count); synchronises the stream."""
+        k = C.c_int(0)
+        st = self._lib.kkt_status_sync(self._h, _stream(stream), C.byref(k))
+        return st, k.value
+
+    # ------------------------------------------------------------- compute
+    def _vec(self, t, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+        return t
+
+    def refactor(self, values: torch.Tensor, stream=None):
+        self._vec(values, "values")
+        if values.numel() != self.nnz:
+            raise ValueError("values has the wrong length")
+        check(self._lib.kkt_refactor(self._h, _ptr(values), _stream(stream)), "kkt_refactor")
+        self._values = values      # the library reads it again in refine
+        self.version += 1
+
+    def solve(self, b: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        self._vec(b, "b")
+        x = torch.empty_like(b) if out is None else out
+        check(self._lib.kkt_solve(self._h, _ptr(b), _ptr(x), _stream(stream)), "kkt_solve")
+        return x
+
+    def solve_transpose(self, g: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        self._vec(g, "g")
+        lam = torch.empty_like(g) if out is None else out
+        check(self._lib.kkt_solve_transpose(self._h, _ptr(g), _ptr(lam), _stream(stream)),
+              "kkt_solve_transpose")
+        return lam
+
+    def _refine(self, fn, b, x, tol, max_it, stream, raise_on_fail):
+        info = _capi.RefineInfo()
+        st = fn(self._h, _ptr(b), _ptr(x), float(tol), int(max_it), C.byref(info), _stream(stream))
+        if raise_on_fail:
+            check(st, "kkt_refine")
+        elif st not in (_capi.KKT_OK, _capi.KKT_ERR_NOT_CONVERGED):
+            check(st, "kkt_refine")
+        return dict(status=st, iters=info.iters, converged=bool(info.converged), omega=info.omega,
+                    history=list(info.omega_hist[: info.n_hist]))
+
+    def refine(self, b, x, tol=0.0, max_it=-1, stream=None, raise_on_fail=False) -> dict:
+        self._vec(b, "b"); self._vec(x, "x")
+        return self._refine(self._lib.kkt_refine, b, x, tol, max_it, stream, raise_on_fail)
+
+    def refine_transpose(self, g, lam, tol=0.0, max_it=-1, stream=None, raise_on_fail=False) -> dict:
+        self._vec(g, "g"); self._vec(lam, "lam")
+        return self._refine(self._lib.kkt_refine_transpose, g, lam, tol, max_it, stream, raise_on_fail)
+
+    def adjoint_gather(self, lam, x, out=None, stream=None) -> torch.Tensor:
+        self._vec(lam, "lam"); self._vec(x, "x")
+        dA = torch.empty(self.nnz, dtype=torch.float64, device=lam.device) if out is None else out
+        check(self._lib.kkt_adjoint_gather(self._h, _ptr(lam), _ptr(x), _ptr(dA), _stream(stream)),
+              "kkt_adjoint_gather")
+        return dA
+
+
+class _KKTSolveFn(torch.autograd.Function):
+    """x = A(values)^-1 b.  Backward reuses the factors of A for the
+    transposed solve lam = A^-T g (refined in FP64) and returns
+    dvalues_k = -lam[row_k] x[col_k] and db = lam."""
+
+    @staticmethod
+    def forward(ctx, solver: KKTSolver, values, b, tol, max_it):
+        solver.refactor(values)
+        x = solver.solve(b)
+        info = solver.refine(b, x, tol, max_it)
+        ctx.solver = solver
+        ctx.version = solver.version
+        ctx.tol, ctx.max_it = tol, max_it
+        ctx.info = info
+        ctx.save_for_backward(values, x)
+        return x
+
+    @staticmethod
+    def backward(ctx, g):
+        solver = ctx.solver
+        values, x = ctx.saved_tensors
+        if solver.version != ctx.version:    # factors were replaced since forward
+            solver.refactor(values)
+        g = g.contiguous()
+        lam = solver.solve_transpose(g)
+        solver.refine_transpose(g, lam, ctx.tol, ctx.max_it)
+        dA = solver.adjoint_gather(lam, x)
+        return None, dA, lam, None, None
+
+
+def kkt_solve(solver: KKTSolver, values: torch.Tensor, b: torch.Tensor, tol: float = 1e-14,
+              max_it: int = 20) -> torch.Tensor:
+    """Differentiable x = A^-1 b for A given by ``values`` on the solver's pattern."""
+    return _KKTSolveFn.apply(solver, values, b, tol, max_it)
