@@ -214,6 +214,35 @@ kkt_status kkt_export_factors(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
 /* Copy the current scaling s (n float64, original indexing) to out_dev. */
 kkt_status kkt_export_scaling(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
 
+/*
+ * Scaled residual without any device allocation and without a context.
+ *
+ * The paper has no counterpart of this call; it exists for callers that cannot
+ * allocate device memory where they need the residual: work recorded inside
+ * CUDA stream capture (allocation is not allowed while a capture is active), or
+ * programs that fix their device-memory budget at start-up.  Such callers may
+ * not be able to create a kkt_ctx either, since kkt_analyze allocates.
+ *
+ * Computes rho = b - A x (FP64, same per-row arithmetic as kkt_refine) and
+ *   out_dev[0] = omega = ||rho||_inf / (||A||_inf ||x||_inf + ||b||_inf),
+ *   out_dev[1..4] = ||rho||_inf, ||x||_inf, ||b||_inf, ||A||_inf.
+ *   n, row_ptr_dev[n+1], col_idx_dev[nnz], values_dev[nnz]: the matrix in CSR
+ *   on the current device; b_dev, x_dev, rho_dev: n float64; out_dev: 5 float64.
+ * Asynchronous on stream, on the calling thread's current device.
+ *
+ * Its only scratch is a fixed 4 MiB array compiled into the library (one
+ * partial result per 32 rows), so n may not exceed 4,194,304: larger n returns
+ * KKT_ERR_ARG and launches nothing.  The array's device address is looked up
+ * the first time the call runs on a device, so make that first call before any
+ * stream capture.  All calls on a device share the array and it keeps the last
+ * call's contents; calls that overlap on the GPU race on it, so order them on
+ * one stream.
+ */
+kkt_status kkt_scaled_residual_noalloc(int n, const int *row_ptr_dev, const int *col_idx_dev,
+                                       const double *values_dev, const double *b_dev,
+                                       const double *x_dev, double *rho_dev, double *out_dev,
+                                       kkt_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

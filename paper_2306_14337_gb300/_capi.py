@@ -101,6 +101,7 @@ SIGNATURES = {
     "kkt_export_symbolic": (C.c_int, [_vp, _ip, _ip, _ip, _ip, _ip]),
     "kkt_export_factors": (C.c_int, [_vp, _vp, _vp]),
     "kkt_export_scaling": (C.c_int, [_vp, _vp, _vp]),
+    "kkt_scaled_residual_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
