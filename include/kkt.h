@@ -85,6 +85,11 @@ typedef struct {
     int cta_warps;          /* warps per CTA of the persistent kernels (1..8; 0 = 8) */
     int refactor_ctas;      /* CTAs of the refactorization (0 = all that fit at once) */
     int solve_ctas;         /* CTAs of the triangular solves (0 = 2 per SM) */
+    size_t update_map_budget; /* bytes allowed for the refactorization's update maps
+                                 (relative positions of every multiply-add; 0 = 1 GiB);
+                                 over budget the kernel searches each row instead */
+    int trace;              /* 1: record per work item claim/completion times on the
+                               device (see kkt_export_trace) */
 } kkt_options;
 
 typedef struct {
@@ -107,6 +112,9 @@ typedef struct {
     double last_omega;      /* scaled residual after the last kkt_refine */
     int factor_fp32;
     long long kernel_launches; /* CUDA kernels this context has launched so far */
+    long long update_map_entries; /* 0 when the update maps are not built */
+    int n_tasks;            /* longest-path tasks of the triangular solves */
+    int max_task;           /* rows in the longest task */
 } kkt_stats;
 
 typedef struct {
@@ -202,14 +210,29 @@ kkt_status kkt_get_stats(const kkt_ctx *ctx, kkt_stats *stats);
  *   perm[n] (new -> old), lu_row_ptr[n+1], lu_col_idx[nnz_lu] (pattern of
  *   combined L+U of the permuted matrix, row-wise, sorted),
  *   level[n], level_u[n] (forward and backward level of every permuted row).
+ * Everything is numbered by perm, the ordering given (KKT_ORDER_USER) or
+ * computed; internally the rows are also relabelled by a postorder of the
+ * elimination tree, which changes neither the fill nor the levels.
  * Any pointer may be NULL to skip that array.
  */
 kkt_status kkt_export_symbolic(const kkt_ctx *ctx, int *perm, int *lu_row_ptr,
                                int *lu_col_idx, int *level, int *level_u);
 
-/* Copy the current factor values (float64, in lu_col_idx order; L strictly
- * below the diagonal, U on and above it) to out_dev (nnz_lu float64). */
+/* Copy the current factor values (float64, in the lu_col_idx order of
+ * kkt_export_symbolic; L strictly below the diagonal, U on and above it) to
+ * out_dev (nnz_lu float64). */
 kkt_status kkt_export_factors(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
+
+/*
+ * Device trace of the most recent launch of one phase (options.trace = 1):
+ * phase 0 refactorization (work item = row in claim order), 1 forward solve,
+ * 2 backward solve, 3 transposed forward, 4 transposed backward (work item =
+ * task in claim order).  out_host receives 2 words per item, the %globaltimer
+ * value (ns) at claim and at completion; *n_items the number of items copied.
+ * Synchronizes the device.
+ */
+kkt_status kkt_export_trace(kkt_ctx *ctx, int phase, unsigned long long *out_host, long long max_items,
+                            long long *n_items);
 
 /* Copy the current scaling s (n float64, original indexing) to out_dev. */
 kkt_status kkt_export_scaling(kkt_ctx *ctx, double *out_dev, kkt_stream stream);

