@@ -345,6 +345,10 @@ def run_native(args, ws, rank, local):
                "sample": f"{done} whole steps of the {args.workload} sequence, single-threaded, "
                          f"ordering computed once outside the timing"}
 
+    variants = {}
+    if rank == 0 and not args.no_variants:
+        variants = run_variants(dev)
+
     if rank != 0:
         return 0
     us = whole_job_us_per_system(total_s, args.steps, ws)
@@ -395,9 +399,96 @@ def run_native(args, ws, rank, local):
                 "h2d_bytes_per_step": 8 * (nnz + 2 * n), "d2h_bytes_per_step": 8 * (nnz + 2 * n)},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _time_ms(fn, reps=3):
+    """Median device time (ms) of fn() over reps runs after one warm-up, CUDA
+    events on the current stream, L2 flushed before each run."""
+    import torch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=torch.cuda.current_device())
+    out = []
+    fn()
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def run_variants(dev):
+    """The batched and FP32 forms against the plain FP64 path on the same GPU,
+    all refined to scaled residual <= 1e-14 (per system, microseconds):
+      batched: 64 scenario systems of the 10,000-bus grid (loads scaled by
+               U(0.8, 1.2)), one batched refactor + solve + refine;
+      fp32:    the 70,000-bus late-IPM system, FP32 factors + FP64 refinement."""
+    import torch
+    from kktgen import config_sequence
+    from paper_2306_14337_gb300 import KKTSolver
+    res = {}
+    # batched, 10,000-bus x 64
+    s = config_sequence(2)
+    k, B = 2, 64
+    vals = torch.tensor(np.stack([s.values(k, sc) for sc in range(1, B + 1)], axis=1), device=dev)
+    bs = torch.tensor(np.stack([s.csr(k, sc) @ s.x_true(k, sc) for sc in range(1, B + 1)], axis=1),
+                      device=dev)
+    Sb = KKTSolver(s.n, s.indptr, s.indices, max_batch=B)
+    xb = torch.empty_like(bs)
+    info = {}
+
+    def batched():
+        Sb.batch_refactor(vals)
+        Sb.batch_solve(bs, out=xb)
+        info["r"] = Sb.batch_refine(bs, xb, 1e-14, 40)
+    tb = _time_ms(batched)
+    S1 = KKTSolver(s.n, s.indptr, s.indices)
+    v1 = vals[:, 0].contiguous()
+    b1 = bs[:, 0].contiguous()
+    x1 = torch.empty_like(b1)
+    info1 = {}
+
+    def plain():
+        S1.refactor(v1)
+        S1.solve(b1, out=x1)
+        info1["r"] = S1.refine(b1, x1, 1e-14, 20)
+    tp = _time_ms(plain)
+    res["batched_10000bus_x64_fp64"] = {
+        "us_per_system": tb * 1e3 / B, "plain_fp64_us_per_system": tp * 1e3,
+        "speedup_vs_plain": tp * B / tb, "omega_max": float(np.max(info["r"]["omega"])),
+        "refine_iters": info["r"]["iters"], "n": s.n, "batch": B}
+    del Sb, S1, vals, bs
+    # FP32 factors + FP64 refinement, 70,000-bus
+    s = config_sequence(3)
+    v = torch.tensor(s.values(0), device=dev)
+    b = torch.tensor(s.rhs(0), device=dev)
+    out = {}
+    for fp32 in (True, False):
+        S = KKTSolver(s.n, s.indptr, s.indices, fp32=fp32, refine_mode="auto")
+        x = torch.empty_like(b)
+        inf = {}
+
+        def run():
+            S.refactor(v)
+            S.solve(b, out=x)
+            inf["r"] = S.refine(b, x, 1e-14, 20)
+        t = _time_ms(run, reps=2)
+        out["fp32" if fp32 else "fp64"] = (t, inf["r"], S.stats())
+        del S
+    t32, r32, st = out["fp32"]
+    t64, r64, _ = out["fp64"]
+    res["fp32_refined_70000bus"] = {
+        "us_per_system": t32 * 1e3, "plain_fp64_us_per_system": t64 * 1e3,
+        "speedup_vs_plain": t64 / t32, "omega": r32["omega"], "refine_iters": r32["iters"],
+        "fp64_omega": r64["omega"], "n": s.n, "nnz_lu": st["nnz_lu"], "levels": st["n_levels"],
+        "hbm_gbs_refactor_solve_fp32": (st["bytes_refactor"] + st["bytes_solve"]) / (t32 * 1e-3) / 1e9}
+    return res
 
 
 def main(argv=None):
@@ -409,6 +500,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2000bus_fp64_adjoint")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the batched and FP32 comparisons (about a minute)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -90,6 +90,10 @@ typedef struct {
                                  over budget the kernel searches each row instead */
     int trace;              /* 1: record per work item claim/completion times on the
                                device (see kkt_export_trace) */
+    int unpublished_row;    /* failure-detection testing only (-1 = off): the
+                               refactorization never publishes this row (numbered
+                               like kkt_export_symbolic), so the rows that depend on
+                               it exhaust spin_limit and report KKT_ERR_TIMEOUT */
 } kkt_options;
 
 typedef struct {
@@ -236,6 +240,29 @@ kkt_status kkt_export_trace(kkt_ctx *ctx, int phase, unsigned long long *out_hos
 
 /* Copy the current scaling s (n float64, original indexing) to out_dev. */
 kkt_status kkt_export_scaling(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
+
+/*
+ * Batched same-pattern systems (configuration option max_batch >= B).  All
+ * arrays are batch innermost: entry k of system s at k * B + s for values
+ * (nnz x B), entry i of system s at i * B + s for vectors (n x B).  One warp
+ * works on one row or task for 32 systems, one system per lane, so that every
+ * access is coalesced across the batch and each FP64 instruction serves 32
+ * systems.  Refinement is classic (Sec. 5.1) and stops when every system
+ * reaches tol; omega_host (B doubles, may be NULL) receives each system's
+ * scaled residual and *iters the solves used.
+ */
+kkt_status kkt_batch_refactor(kkt_ctx *ctx, int B, const double *values_dev, kkt_stream stream);
+kkt_status kkt_batch_solve(kkt_ctx *ctx, int B, const double *b_dev, double *x_dev, kkt_stream stream);
+kkt_status kkt_batch_solve_transpose(kkt_ctx *ctx, int B, const double *g_dev, double *lam_dev,
+                                     kkt_stream stream);
+kkt_status kkt_batch_refine(kkt_ctx *ctx, int B, const double *b_dev, double *x_dev, double tol,
+                            int max_it, double *omega_host, int *iters, kkt_stream stream);
+kkt_status kkt_batch_refine_transpose(kkt_ctx *ctx, int B, const double *g_dev, double *lam_dev,
+                                      double tol, int max_it, double *omega_host, int *iters,
+                                      kkt_stream stream);
+/* Factor values of one system of the last batched refactorization, in the
+ * order of kkt_export_factors. */
+kkt_status kkt_batch_export_factors(kkt_ctx *ctx, int sys, double *out_dev, kkt_stream stream);
 
 /*
  * Scaled residual without any device allocation and without a context.

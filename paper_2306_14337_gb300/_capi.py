@@ -46,6 +46,7 @@ class Options(C.Structure):
         ("solve_ctas", C.c_int),
         ("update_map_budget", C.c_size_t),
         ("trace", C.c_int),
+        ("unpublished_row", C.c_int),
     ]
 
 
@@ -108,6 +109,14 @@ SIGNATURES = {
     "kkt_export_scaling": (C.c_int, [_vp, _vp, _vp]),
     "kkt_export_trace": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_ulonglong), C.c_longlong,
                                    C.POINTER(C.c_longlong)]),
+    "kkt_batch_refactor": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "kkt_batch_solve": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "kkt_batch_solve_transpose": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "kkt_batch_refine": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_double, C.c_int, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int), _vp]),
+    "kkt_batch_refine_transpose": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_double, C.c_int,
+                                             C.POINTER(C.c_double), C.POINTER(C.c_int), _vp]),
+    "kkt_batch_export_factors": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "kkt_scaled_residual_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 

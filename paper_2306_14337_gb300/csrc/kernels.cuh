@@ -51,6 +51,7 @@ struct TaskCfg {
     int cap;                             // task results kept in shared memory per warp
     const int *task_lo, *task_hi;        // rows of task t: [lo, hi], bottom to top
     const int *order_f, *order_b;        // claim orders of the forward / backward phases
+    const int *order_topo;               // forward order without the longest-first prefix
 };
 
 struct RunCfg {
@@ -63,6 +64,7 @@ struct RunCfg {
     int scratch_stride;          // entries per warp in scratch
     unsigned long long *trace;   // optional: per work item {claim, done} %globaltimer (ns)
     long long trace_stride;      // words per phase region
+    int unpublished_row;         // failure-detection test: this row is never published (-1: none)
 };
 
 // Trace regions, one per phase, each (max work items) x 2 words.

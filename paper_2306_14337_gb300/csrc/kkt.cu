@@ -390,7 +390,7 @@ k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const doubl
         for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + rb + t, w[t]);
         if (lane == 0) {
             LU[rb + dp] = w[dp];
-            publish(rc, rcp + i, T(1) / w[dp]);
+            if (i != rc.unpublished_row) publish(rc, rcp + i, T(1) / w[dp]);
         }
         for (int t = lane; t < len; t += 32) {
             if (t < dp) LU[rb + t] = w[t];
@@ -699,11 +699,305 @@ __global__ void k_vscale(double *__restrict__ v, const double *__restrict__ w, d
     if (i < n) v[i] = w[i] * s;
 }
 
+// ===========================================================================
+// Batched same-pattern systems (batch innermost): value k of system s sits at
+// k * B + s, vector entry i of system s at i * B + s.  One warp handles one
+// row (refactorization) or one task (solves) for 32 systems, one system per
+// lane; every lane runs its system's elimination sequentially, so an FP64
+// instruction serves 32 systems and every access is coalesced across the
+// batch.  Work items are (row or task, group of 32 systems), claimed in
+// topological order.
+
+__device__ __forceinline__ double ld_acquire_v(const double *p) {
+    double v;
+    asm volatile("ld.acquire.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ float ld_acquire_v(const float *p) {
+    float v;
+    asm volatile("ld.acquire.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_v(double *p, double v) {
+    asm volatile("st.release.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_v(float *p, float v) {
+    asm volatile("st.release.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+// Like warp_wait_load, with acquire semantics on the value each lane finally
+// reads (the producer releases it after writing the data it guards).
+template <typename T>
+__device__ __forceinline__ T warp_wait_acquire(const RunCfg &rc, const T *p, bool need, int lane) {
+    T v = need ? ld_acquire_v(p) : T(0);
+    unsigned pend = __ballot_sync(FULL, need && is_marker(v));
+    while (pend) {
+        const int leader = __ffs(pend) - 1;
+        int bad = 0;
+        if (lane == leader) {
+            unsigned ns = 32;
+            long long it = 0;
+            for (;;) {
+                __nanosleep(ns);
+                v = ld_relaxed_v(p);
+                if (!is_marker(v)) break;
+                if (ns < 1024) ns <<= 1;
+                if ((++it & 7) == 0) {
+                    if (ld_relaxed(rc.status + ST_ABORT)) { bad = 1; break; }
+                    if (it > rc.spin_limit) {
+                        atomicExch(rc.status + ST_TIMEOUT, 1);
+                        atomicExch(rc.status + ST_ABORT, 1);
+                        bad = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        if (__shfl_sync(FULL, bad, leader)) {
+            if (is_marker(v)) v = T(0);
+            break;
+        }
+        if ((pend >> lane) & 1u) v = ld_acquire_v(p);
+        pend = __ballot_sync(FULL, ((pend >> lane) & 1u) && is_marker(v));
+    }
+    return v;
+}
+
+// per-(row, system) scaling, ||A||_inf per system
+__global__ void k_bscale(DevPattern P, int B, const double *__restrict__ aval, double *__restrict__ s_orig,
+                         double *__restrict__ sp, unsigned long long *norms, int *status, int equil) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)P.n * B) return;
+    const int r = (int)(gid / B), sy = (int)(gid % B);
+    double rmax = 0.0, rsum = 0.0;
+    bool bad = false;
+    for (int p = P.a_rp[r]; p < P.a_rp[r + 1]; p++) {
+        const double a = fabs(aval[(long long)p * B + sy]);
+        if (!isfinite(a)) bad = true;
+        rmax = fmax(rmax, a);
+        rsum += a;
+    }
+    double s = 1.0;
+    if (equil && !bad && rmax > 0.0) s = ldexp(1.0, -floor_half(ilogb(rmax)));
+    s_orig[(long long)r * B + sy] = s;
+    sp[(long long)P.iperm[r] * B + sy] = s;
+    if (bad) atomicExch(status + ST_NONFINITE, 1);
+    else atomic_max_nonneg(norms + (long long)NM_ANORM * B + sy, rsum);
+}
+
+__global__ void k_bamax(DevPattern P, int B, const double *__restrict__ aval, const double *__restrict__ s_orig,
+                        unsigned long long *norms) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)P.n * B) return;
+    const int r = (int)(gid / B), sy = (int)(gid % B);
+    const double sr = s_orig[(long long)r * B + sy];
+    double m = 0.0, csum = 0.0;
+    for (int p = P.a_rp[r]; p < P.a_rp[r + 1]; p++)
+        m = fmax(m, fabs(aval[(long long)p * B + sy]) * sr * s_orig[(long long)P.a_ci[p] * B + sy]);
+    for (int q = P.at_rp[r]; q < P.at_rp[r + 1]; q++) csum += fabs(aval[(long long)P.at_src[q] * B + sy]);
+    if (isfinite(m)) atomic_max_nonneg(norms + (long long)NM_AMAX * B + sy, m);
+    if (isfinite(csum)) atomic_max_nonneg(norms + (long long)NM_A1NORM * B + sy, csum);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(WARPS * 32, 2)
+k_brefactor(DevPattern P, RunCfg rc, int B, const double *__restrict__ aval, const double *__restrict__ sp,
+            const unsigned long long *__restrict__ norms, T *LU, T *LUT, T *rcp, double tau_rel) {
+    const int lane = threadIdx.x & 31;
+    const int G = (B + 31) >> 5;
+    const int e = rc.sched->epoch + 1;
+    const bool mapped = P.upd_off != nullptr;
+    for (;;) {
+        const int slot = claim_row(rc, lane);
+        if (slot >= P.n * G) break;
+        const int i = P.order_f[slot / G];
+        const int sy = (slot % G) * 32 + lane;
+        const bool act = sy < B;
+        const int sy_ = act ? sy : 0;
+        const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
+        const double si = sp[(long long)i * B + sy_];
+        const double tau = tau_rel * __longlong_as_double((long long)norms[(long long)NM_AMAX * B + sy_]);
+        T *w = LU + (long long)rb * B + sy_;                 // this system's row, stride B
+        for (int t = 0; t < len; t++) {
+            const int k = P.src[rb + t];
+            const double v = (k >= 0 && act) ? si * sp[(long long)P.lu_ci[rb + t] * B + sy_] *
+                                                   aval[(long long)k * B + sy_]
+                                             : 0.0;
+            if (act) w[(long long)t * B] = (T)v;
+        }
+        for (int t = 0; t < dp; t++) {
+            const int d = P.lu_ci[rb + t];
+            const int ub = P.diag[d], ue = P.lu_rp[d + 1];
+            const unsigned mo = mapped ? P.upd_off[rb + t] : 0u;
+            const T r = warp_wait_acquire(rc, rcp + (long long)d * B + sy_, act, lane);
+            if (!act) continue;
+            const T l = w[(long long)t * B] * r;
+            const T *ud = LU + sy_;
+            // the targets of one pivot step are distinct: eight updates at a
+            // time, all loads issued before the stores (memory-level parallelism)
+            for (int u0 = ub + 1; u0 < ue; u0 += 8) {
+                int lo[8];
+                T a[8], x[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int u = u0 + q;
+                    lo[q] = -1;
+                    if (u < ue) {
+                        if (mapped) {
+                            lo[q] = P.upd_map[mo + (u - ub - 1)];
+                        } else {
+                            const int j = P.lu_ci[u];
+                            int a_ = t + 1, b_ = len;
+                            while (a_ < b_) {
+                                const int mid = (a_ + b_) >> 1;
+                                if (P.lu_ci[rb + mid] < j) a_ = mid + 1; else b_ = mid;
+                            }
+                            if (a_ < len && P.lu_ci[rb + a_] == j) lo[q] = a_;
+                            else atomicExch(rc.status + ST_INTERNAL, 1);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    a[q] = lo[q] >= 0 ? ud[(long long)(u0 + q) * B] : T(0);
+                    x[q] = lo[q] >= 0 ? w[(long long)lo[q] * B] : T(0);
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++)
+                    if (lo[q] >= 0) w[(long long)lo[q] * B] = x[q] - l * a[q];
+            }
+            w[(long long)t * B] = l;
+        }
+        if (act) {
+            double pv = (double)w[(long long)dp * B];
+            if (!(fabs(pv) >= tau) || isinf(pv)) {
+                const int k = P.src[rb + dp];
+                const double aii = (k >= 0) ? si * si * aval[(long long)k * B + sy_] : 0.0;
+                if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
+                pv = (aii < 0.0) ? -tau : tau;
+                atomicAdd(rc.status + ST_PERTURBED, 1);
+            }
+            w[(long long)dp * B] = (T)pv;
+            for (int t = 0; t < len; t++) LUT[(long long)P.tpos[rb + t] * B + sy_] = w[(long long)t * B];
+            T rv = T(1) / (T)pv;
+            if (is_marker(rv)) rv = T(NAN);
+            st_release_v(rcp + (long long)i * B + sy_, rv);   // orders this lane's row stores before it
+        }
+    }
+    if (lane == 0) finish_launch(rc, e);
+}
+
+// Batched triangular solves over tasks (see k_trisolve for the phases).
+template <typename T, bool BACKWARD, bool TRANS>
+__global__ void __launch_bounds__(WARPS * 32, 2)
+k_btrisolve(DevPattern P, RunCfg rc, TaskCfg tk, int B, const T *__restrict__ F, const T *__restrict__ rcp,
+            const double *__restrict__ rhs, const double *__restrict__ sp, const T *__restrict__ yin, T *yout,
+            double *__restrict__ out, int accumulate) {
+    const int lane = threadIdx.x & 31;
+    const int G = (B + 31) >> 5;
+    const int e = rc.sched->epoch + 1;
+    const int *order = BACKWARD ? tk.order_b : tk.order_topo;
+    constexpr bool DIV = (TRANS != BACKWARD);
+    for (;;) {
+        const int slot = claim_row(rc, lane);
+        if (slot >= tk.ntasks * G) break;
+        const int tid = order[slot / G];
+        const int sy = (slot % G) * 32 + lane;
+        const bool act = sy < B;
+        const int sy_ = act ? sy : 0;
+        const int lo = tk.task_lo[tid], hi = tk.task_hi[tid];
+        const int m = hi - lo + 1;
+        for (int k = 0; k < m; k++) {
+            const int i = BACKWARD ? hi - k : lo + k;
+            const int dg = P.diag[i];
+            const int tb = BACKWARD ? dg + 1 : P.lu_rp[i];
+            const int te = BACKWARD ? P.lu_rp[i + 1] : dg;
+            T acc = 0;
+            for (int t0 = tb; t0 < te; t0 += 8) {
+                T a[8], v[8];
+                int c[8];
+                unsigned need = 0;
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int t = t0 + q;
+                    a[q] = T(0);
+                    v[q] = T(0);
+                    c[q] = 0;
+                    if (t < te) {
+                        c[q] = P.lu_ci[t];
+                        a[q] = F[(long long)t * B + sy_];
+                        v[q] = ld_relaxed_v(yout + (long long)c[q] * B + sy_);
+                        if (act && is_marker(v[q])) need |= 1u << q;
+                    }
+                }
+                if (__any_sync(FULL, need != 0)) {
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const bool nq = (need >> q) & 1u;
+                        const T w = warp_wait_load(rc, yout + (long long)c[q] * B + sy_, nq, lane);
+                        if (nq) v[q] = w;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; q++) acc += a[q] * v[q];
+            }
+            if (act) {
+                T r = (BACKWARD ? yin[(long long)i * B + sy] : (T)(sp[(long long)i * B + sy] *
+                                                                   rhs[(long long)P.perm[i] * B + sy])) - acc;
+                if (DIV) r = r * rcp[(long long)i * B + sy];
+                if (is_marker(r)) {
+                    r = T(NAN);
+                    atomicExch(rc.status + ST_NONFINITE, 1);
+                }
+                st_relaxed_v(yout + (long long)i * B + sy, r);
+                if (BACKWARD) {
+                    const long long o = (long long)P.perm[i] * B + sy;
+                    const double w = sp[(long long)i * B + sy] * (double)r;
+                    out[o] = accumulate ? out[o] + w : w;
+                }
+            }
+        }
+    }
+    if (lane == 0) finish_launch(rc, e);
+}
+
+// rho = b - A x (or A^T x) per system, with per-system norms
+__global__ void k_bresid(DevPattern P, int B, const double *__restrict__ aval, const double *__restrict__ b,
+                         const double *__restrict__ x, double *__restrict__ rho, unsigned long long *norms,
+                         int transpose) {
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)P.n * B) return;
+    const int r = (int)(gid / B), sy = (int)(gid % B);
+    double acc = 0.0;
+    if (!transpose) {
+        for (int p = P.a_rp[r]; p < P.a_rp[r + 1]; p++)
+            acc += aval[(long long)p * B + sy] * x[(long long)P.a_ci[p] * B + sy];
+    } else {
+        for (int q = P.at_rp[r]; q < P.at_rp[r + 1]; q++) {
+            const int k = P.at_src[q];
+            acc += aval[(long long)k * B + sy] * x[(long long)P.a_row[k] * B + sy];
+        }
+    }
+    const double br = b[gid];
+    const double rv = br - acc;
+    rho[gid] = rv;
+    atomic_max_nonneg(norms + (long long)NM_RMAX * B + sy, fabs(rv));
+    atomic_max_nonneg(norms + (long long)NM_XMAX * B + sy, fabs(x[gid]));
+    atomic_max_nonneg(norms + (long long)NM_BMAX * B + sy, fabs(br));
+}
+
 // dA_k = -lam[row_k] x[col_k]
 __global__ void k_adjoint(DevPattern P, const double *__restrict__ lam, const double *__restrict__ x,
                           double *__restrict__ dA) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < P.nnz_a) dA[k] = -lam[P.a_row[k]] * x[P.a_ci[k]];
+}
+
+template <typename T>
+__global__ void k_bexport(const T *__restrict__ LU, const int *__restrict__ slot, int B, int sys,
+                          double *__restrict__ out, long long m) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) out[k] = (double)LU[(long long)slot[k] * B + sys];
 }
 
 template <typename T>
@@ -745,6 +1039,14 @@ struct kkt_ctx {
     // partial dots, coefficients
     double *d_krylov = nullptr;
     int kry_m = 0, kry_blocks = 0;
+    // batched workspace (capacity max_batch): factors, transposed factors,
+    // reciprocal pivots, scaling, work vectors and norms, batch innermost
+    int bcap = 0;
+    void *b_lu = nullptr, *b_lut = nullptr, *b_rcp = nullptr, *b_y = nullptr;
+    double *b_s = nullptr, *b_sp = nullptr, *b_rho = nullptr;
+    unsigned long long *b_norms = nullptr, *hb_norms = nullptr;
+    const double *b_values = nullptr;
+    int b_factored = 0;
     int *d_view_slot = nullptr;
     TaskCfg tk{};
     size_t solve_smem = 0;
@@ -812,6 +1114,7 @@ void kkt_default_options(kkt_options *o) {
     o->solve_ctas = 0;
     o->update_map_budget = 0;
     o->trace = 0;
+    o->unpublished_row = -1;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -971,14 +1274,19 @@ static kkt_status upload(kkt_ctx *c) {
             return top[x] < top[y];
         });
         std::stable_sort(ob.begin(), ob.end(), [&](int x, int y) { return top[x] > top[y]; });
+        std::vector<int> ot(nt);
+        std::iota(ot.begin(), ot.end(), 0);
+        std::stable_sort(ot.begin(), ot.end(), [&](int x, int y) { return top[x] < top[y]; });
         int *d = nullptr;
-        CK(cudaMalloc(&d, 2 * (size_t)nt * sizeof(int)));
+        CK(cudaMalloc(&d, 3 * (size_t)nt * sizeof(int)));
         CK(cudaMemcpy(d, of.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(d + nt, ob.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(d + 2 * nt, ot.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
         c->d_task_orders = d;
         c->tk.ntasks = nt;
         c->tk.order_f = d;
         c->tk.order_b = d + nt;
+        c->tk.order_topo = d + 2 * nt;
         c->tk.cap = std::min(a.max_task, 1024);
         c->solve_smem = (size_t)nw * c->tk.cap * tsz;
         c->device_bytes += 2 * (size_t)nt * sizeof(int);
@@ -1005,6 +1313,25 @@ static kkt_status upload(kkt_ctx *c) {
         CK(cudaMalloc(&c->d_krylov, words * sizeof(double)));
         c->device_bytes += words * sizeof(double);
     }
+    if (c->opt.max_batch > 1) {
+        const size_t Bc = (size_t)c->opt.max_batch;
+        c->bcap = c->opt.max_batch;
+        CK(cudaMalloc(&c->b_lu, nlu * Bc * tsz));
+        CK(cudaMalloc(&c->b_lut, nlu * Bc * tsz));
+        CK(cudaMalloc(&c->b_rcp, (size_t)n * Bc * tsz));
+        CK(cudaMalloc(&c->b_y, 2 * (size_t)n * Bc * tsz));
+        CK(cudaMalloc(&c->b_s, (size_t)n * Bc * sizeof(double)));
+        CK(cudaMalloc(&c->b_sp, (size_t)n * Bc * sizeof(double)));
+        CK(cudaMalloc(&c->b_rho, (size_t)n * Bc * sizeof(double)));
+        CK(cudaMalloc(&c->b_norms, NM_WORDS * Bc * sizeof(unsigned long long)));
+        CK(cudaMallocHost(&c->hb_norms, NM_WORDS * Bc * sizeof(unsigned long long)));
+        c->device_bytes += (2 * nlu + 3 * (size_t)n) * Bc * tsz + 3 * (size_t)n * Bc * sizeof(double);
+        if (f32) {
+            CK(cudaFuncSetAttribute(k_brefactor<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        } else {
+            CK(cudaFuncSetAttribute(k_brefactor<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        }
+    }
     if (c->opt.trace) {
         const long long items = std::max<long long>(n, c->tk.ntasks);
         c->rc.trace_stride = 2 * items;
@@ -1013,6 +1340,9 @@ static kkt_status upload(kkt_ctx *c) {
         c->rc.trace = c->d_trace;
     }
     c->rc.spin_limit = c->opt.spin_limit;
+    c->rc.unpublished_row = -1;
+    if (c->opt.unpublished_row >= 0 && c->opt.unpublished_row < n)
+        c->rc.unpublished_row = a.internal_of[c->opt.unpublished_row];
     c->rc.status = c->d_status;
     c->rc.norms = c->d_norms;
     c->rc.sched = c->d_sched;
@@ -1041,6 +1371,15 @@ void kkt_destroy(kkt_ctx *c) {
         cudaFree(c->d_trace);
         cudaFree(c->d_view_slot);
         cudaFree(c->d_krylov);
+        cudaFree(c->b_lu);
+        cudaFree(c->b_lut);
+        cudaFree(c->b_rcp);
+        cudaFree(c->b_y);
+        cudaFree(c->b_s);
+        cudaFree(c->b_sp);
+        cudaFree(c->b_rho);
+        cudaFree(c->b_norms);
+        cudaFreeHost(c->hb_norms);
         cudaFree(c->d_scratch);
         cudaFreeHost(c->h_norms);
     }
@@ -1396,6 +1735,195 @@ kkt_status kkt_refine_transpose(kkt_ctx *c, const double *g_dev, double *lam_dev
     if (!c->factored) return KKT_ERR_STATE;
     DeviceGuard g(c->dev);
     return refine_any(c, g_dev, lam_dev, tol, max_it, info, 1, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// batched entry points
+
+static void ensure_view(const kkt_ctx *c);
+
+#define REQUIRE_BATCH(c, B)                                                                  \
+    do {                                                                                     \
+        REQUIRE_DEVICE(c);                                                                   \
+        if ((B) < 1 || (B) > (c)->bcap) {                                                    \
+            g_last_error = "batch size outside 1..max_batch (set max_batch at analysis)";    \
+            return KKT_ERR_ARG;                                                              \
+        }                                                                                    \
+    } while (0)
+
+template <typename T> static kkt_status launch_brefactor(kkt_ctx *c, int B, cudaStream_t s) {
+    const int n = c->an.n;
+    CK(cudaMemsetAsync(c->b_rcp, 0xff, (size_t)n * B * sizeof(T), s));
+    k_brefactor<T><<<c->grid, c->cta_warps * 32, 0, s>>>(c->P, c->rc, B, c->b_values, c->b_sp, c->b_norms,
+                                                          (T *)c->b_lu, (T *)c->b_lut, (T *)c->b_rcp, c->tau_rel);
+    CK(cudaGetLastError());
+    c->launches++;
+    return KKT_OK;
+}
+
+kkt_status kkt_batch_refactor(kkt_ctx *c, int B, const double *values_dev, kkt_stream stream) {
+    REQUIRE_BATCH(c, B);
+    if (!values_dev) return KKT_ERR_ARG;
+    DeviceGuard g(c->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = c->an.n;
+    c->b_values = values_dev;
+    CK(cudaMemsetAsync(c->b_norms, 0, NM_WORDS * (size_t)B * sizeof(unsigned long long), s));
+    k_bscale<<<blocks_for((long long)n * B, 256), 256, 0, s>>>(c->P, B, values_dev, c->b_s, c->b_sp, c->b_norms,
+                                                              c->d_status, c->opt.equilibrate);
+    CK(cudaGetLastError());
+    c->launches++;
+    k_bamax<<<blocks_for((long long)n * B, 256), 256, 0, s>>>(c->P, B, values_dev, c->b_s, c->b_norms);
+    CK(cudaGetLastError());
+    c->launches++;
+    kkt_status r = c->opt.factor_fp32 ? launch_brefactor<float>(c, B, s) : launch_brefactor<double>(c, B, s);
+    if (r == KKT_OK) c->b_factored = B;
+    return r;
+}
+
+template <typename T>
+static kkt_status launch_bsolve(kkt_ctx *c, int B, const double *b, double *x, int accumulate, int transpose,
+                                cudaStream_t s) {
+    const int n = c->an.n;
+    T *y = (T *)c->b_y, *z = y + (size_t)n * B;
+    const T *F = (const T *)(transpose ? c->b_lut : c->b_lu), *R = (const T *)c->b_rcp;
+    CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * B * sizeof(T), s));
+    if (transpose) {
+        k_btrisolve<T, false, true><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(
+            c->P, c->rc, c->tk, B, F, R, b, c->b_sp, nullptr, y, nullptr, 0);
+        CK(cudaGetLastError());
+        c->launches++;
+        k_btrisolve<T, true, true><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(
+            c->P, c->rc, c->tk, B, F, R, nullptr, c->b_sp, y, z, x, accumulate);
+    } else {
+        k_btrisolve<T, false, false><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(
+            c->P, c->rc, c->tk, B, F, R, b, c->b_sp, nullptr, y, nullptr, 0);
+        CK(cudaGetLastError());
+        c->launches++;
+        k_btrisolve<T, true, false><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(
+            c->P, c->rc, c->tk, B, F, R, nullptr, c->b_sp, y, z, x, accumulate);
+    }
+    CK(cudaGetLastError());
+    c->launches++;
+    return KKT_OK;
+}
+
+static kkt_status bsolve_any(kkt_ctx *c, int B, const double *b, double *x, int accumulate, int transpose,
+                             cudaStream_t s) {
+    return c->opt.factor_fp32 ? launch_bsolve<float>(c, B, b, x, accumulate, transpose, s)
+                              : launch_bsolve<double>(c, B, b, x, accumulate, transpose, s);
+}
+
+kkt_status kkt_batch_solve(kkt_ctx *c, int B, const double *b_dev, double *x_dev, kkt_stream stream) {
+    REQUIRE_BATCH(c, B);
+    if (!b_dev || !x_dev || b_dev == x_dev) return KKT_ERR_ARG;
+    if (c->b_factored != B) return KKT_ERR_STATE;
+    DeviceGuard g(c->dev);
+    return bsolve_any(c, B, b_dev, x_dev, 0, 0, (cudaStream_t)stream);
+}
+
+kkt_status kkt_batch_solve_transpose(kkt_ctx *c, int B, const double *g_dev, double *lam_dev,
+                                     kkt_stream stream) {
+    REQUIRE_BATCH(c, B);
+    if (!g_dev || !lam_dev || g_dev == lam_dev) return KKT_ERR_ARG;
+    if (c->b_factored != B) return KKT_ERR_STATE;
+    DeviceGuard g(c->dev);
+    return bsolve_any(c, B, g_dev, lam_dev, 0, 1, (cudaStream_t)stream);
+}
+
+static kkt_status bresidual_omega(kkt_ctx *c, int B, const double *b, const double *x, int transpose,
+                                  cudaStream_t s, double *omega) {
+    const int n = c->an.n;
+    for (int k = NM_RMAX; k <= NM_BMAX; k++)
+        CK(cudaMemsetAsync(c->b_norms + (size_t)k * B, 0, B * sizeof(unsigned long long), s));
+    k_bresid<<<blocks_for((long long)n * B, 256), 256, 0, s>>>(c->P, B, c->b_values, b, x, c->b_rho, c->b_norms,
+                                                              transpose);
+    CK(cudaGetLastError());
+    c->launches++;
+    CK(cudaMemcpyAsync(c->hb_norms, c->b_norms, NM_WORDS * (size_t)B * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    auto val = [&](int k, int sy) {
+        double v;
+        std::memcpy(&v, &c->hb_norms[(size_t)k * B + sy], sizeof(v));
+        return v;
+    };
+    for (int sy = 0; sy < B; sy++) {
+        const double an = val(transpose ? NM_A1NORM : NM_ANORM, sy);
+        const double den = an * val(NM_XMAX, sy) + val(NM_BMAX, sy);
+        const double r = val(NM_RMAX, sy);
+        omega[sy] = den > 0 ? r / den : (r > 0 ? INFINITY : 0.0);
+    }
+    return KKT_OK;
+}
+
+static kkt_status brefine_any(kkt_ctx *c, int B, const double *b, double *x, double tol, int max_it,
+                              double *omega_host, int *iters, int transpose, cudaStream_t s) {
+    if (tol <= 0) tol = c->opt.tol;
+    if (max_it < 0) max_it = c->opt.max_refine;
+    std::vector<double> w(B);
+    kkt_status st = bresidual_omega(c, B, b, x, transpose, s, w.data());
+    if (st) return st;
+    int it = 0;
+    auto worst = [&]() {
+        double m = 0.0;
+        for (double v : w) m = std::isfinite(v) ? std::max(m, v) : INFINITY;
+        return m;
+    };
+    while (!(worst() <= tol) && it < max_it && std::isfinite(worst())) {
+        st = bsolve_any(c, B, c->b_rho, x, 1, transpose, s);
+        if (st) return st;
+        it++;
+        st = bresidual_omega(c, B, b, x, transpose, s, w.data());
+        if (st) return st;
+    }
+    if (omega_host) std::memcpy(omega_host, w.data(), B * sizeof(double));
+    if (iters) *iters = it;
+    int dst[ST_WORDS];
+    CK(cudaMemcpy(dst, c->d_status, sizeof(dst), cudaMemcpyDeviceToHost));
+    if (dst[ST_TIMEOUT]) return KKT_ERR_TIMEOUT;
+    return worst() <= tol ? KKT_OK : KKT_ERR_NOT_CONVERGED;
+}
+
+kkt_status kkt_batch_refine(kkt_ctx *c, int B, const double *b_dev, double *x_dev, double tol, int max_it,
+                            double *omega_host, int *iters, kkt_stream stream) {
+    REQUIRE_BATCH(c, B);
+    if (!b_dev || !x_dev || b_dev == x_dev) return KKT_ERR_ARG;
+    if (c->b_factored != B) return KKT_ERR_STATE;
+    DeviceGuard g(c->dev);
+    return brefine_any(c, B, b_dev, x_dev, tol, max_it, omega_host, iters, 0, (cudaStream_t)stream);
+}
+
+kkt_status kkt_batch_refine_transpose(kkt_ctx *c, int B, const double *g_dev, double *lam_dev, double tol,
+                                      int max_it, double *omega_host, int *iters, kkt_stream stream) {
+    REQUIRE_BATCH(c, B);
+    if (!g_dev || !lam_dev || g_dev == lam_dev) return KKT_ERR_ARG;
+    if (c->b_factored != B) return KKT_ERR_STATE;
+    DeviceGuard g(c->dev);
+    return brefine_any(c, B, g_dev, lam_dev, tol, max_it, omega_host, iters, 1, (cudaStream_t)stream);
+}
+
+kkt_status kkt_batch_export_factors(kkt_ctx *c, int sys, double *out_dev, kkt_stream stream) {
+    REQUIRE_DEVICE(c);
+    if (!out_dev || sys < 0 || sys >= c->b_factored) return KKT_ERR_ARG;
+    DeviceGuard g(c->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->d_view_slot) {
+        ensure_view(c);
+        CK(cudaMalloc(&c->d_view_slot, c->view_slot.size() * sizeof(int)));
+        CK(cudaMemcpy(c->d_view_slot, c->view_slot.data(), c->view_slot.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
+    }
+    const int B = c->b_factored;
+    if (c->opt.factor_fp32)
+        k_bexport<float><<<blocks_for(c->nnz_lu, 256), 256, 0, s>>>((const float *)c->b_lu, c->d_view_slot, B, sys,
+                                                                    out_dev, c->nnz_lu);
+    else
+        k_bexport<double><<<blocks_for(c->nnz_lu, 256), 256, 0, s>>>((const double *)c->b_lu, c->d_view_slot, B,
+                                                                     sys, out_dev, c->nnz_lu);
+    CK(cudaGetLastError());
+    c->launches++;
+    return KKT_OK;
 }
 
 kkt_status kkt_adjoint_gather(kkt_ctx *c, const double *lam_dev, const double *x_dev, double *dA_dev,

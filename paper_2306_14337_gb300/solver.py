@@ -43,7 +43,8 @@ class KKTSolver:
     def __init__(self, n, indptr, indices, *, fp32=False, equilibrate=True, ordering="amd",
                  perm=None, refine_mode="classic", tol=1e-14, max_refine=20,
                  pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
-                 solve_ctas=0, update_map_budget=0, trace=False, device=0):
+                 solve_ctas=0, update_map_budget=0, trace=False, max_batch=1, unpublished_row=-1,
+                 device=0):
         self._lib = _capi.load()
         self.n = int(n)
         self._rp = _i32(indptr)
@@ -68,6 +69,8 @@ class KKTSolver:
         opt.solve_ctas = int(solve_ctas)
         opt.update_map_budget = int(update_map_budget)
         opt.trace = int(bool(trace))
+        opt.max_batch = int(max_batch)
+        opt.unpublished_row = int(unpublished_row)
         self.device = None if device is None else torch.device("cuda", int(device)) if not isinstance(
             device, torch.device) else device
         opt.device = -1 if self.device is None else (self.device.index or 0)
@@ -185,6 +188,56 @@ class KKTSolver:
         check(self._lib.kkt_adjoint_gather(self._h, _ptr(lam), _ptr(x), _ptr(dA), _stream(stream)),
               "kkt_adjoint_gather")
         return dA
+
+
+    # ------------------------------------------------------- batched systems
+    def _bvec(self, t, rows, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous() and t.dim() == 2 and t.shape[0] == rows):
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor of shape ({rows}, B)")
+        return t.shape[1]
+
+    def batch_refactor(self, values: torch.Tensor, stream=None):
+        """values: (nnz, B), batch innermost."""
+        B = self._bvec(values, self.nnz, "values")
+        check(self._lib.kkt_batch_refactor(self._h, B, _ptr(values), _stream(stream)), "kkt_batch_refactor")
+        self._bvalues = values
+        self.batch = B
+
+    def batch_solve(self, b: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        B = self._bvec(b, self.n, "b")
+        x = torch.empty_like(b) if out is None else out
+        check(self._lib.kkt_batch_solve(self._h, B, _ptr(b), _ptr(x), _stream(stream)), "kkt_batch_solve")
+        return x
+
+    def batch_solve_transpose(self, g: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        B = self._bvec(g, self.n, "g")
+        lam = torch.empty_like(g) if out is None else out
+        check(self._lib.kkt_batch_solve_transpose(self._h, B, _ptr(g), _ptr(lam), _stream(stream)),
+              "kkt_batch_solve_transpose")
+        return lam
+
+    def _brefine(self, fn, b, x, tol, max_it, stream):
+        B = self._bvec(b, self.n, "b")
+        om = np.zeros(B)
+        it = C.c_int(0)
+        st = fn(self._h, B, _ptr(b), _ptr(x), float(tol), int(max_it),
+                om.ctypes.data_as(C.POINTER(C.c_double)), C.byref(it), _stream(stream))
+        if st not in (_capi.KKT_OK, _capi.KKT_ERR_NOT_CONVERGED):
+            check(st, "kkt_batch_refine")
+        return dict(status=st, iters=it.value, omega=om, converged=bool(np.all(om <= (tol or 1e-14))))
+
+    def batch_refine(self, b, x, tol=0.0, max_it=-1, stream=None) -> dict:
+        return self._brefine(self._lib.kkt_batch_refine, b, x, tol, max_it, stream)
+
+    def batch_refine_transpose(self, g, lam, tol=0.0, max_it=-1, stream=None) -> dict:
+        return self._brefine(self._lib.kkt_batch_refine_transpose, g, lam, tol, max_it, stream)
+
+    def batch_export_factors(self, sys: int, stream=None) -> torch.Tensor:
+        out = torch.empty(self.stats()["nnz_lu"], dtype=torch.float64, device=self.device)
+        check(self._lib.kkt_batch_export_factors(self._h, int(sys), _ptr(out), _stream(stream)),
+              "kkt_batch_export_factors")
+        return out
 
 
 class _KKTSolveFn(torch.autograd.Function):
