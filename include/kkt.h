@@ -90,6 +90,8 @@ typedef struct {
                                  over budget the kernel searches each row instead */
     int trace;              /* 1: record per work item claim/completion times on the
                                device (see kkt_export_trace) */
+    int poll_ns_max;        /* backoff cap (ns) of a waiting lane; one lane per warp
+                               polls, doubling its sleep from 32 ns (0 = 128 ns) */
     int unpublished_row;    /* failure-detection testing only (-1 = off): the
                                refactorization never publishes this row (numbered
                                like kkt_export_symbolic), so the rows that depend on

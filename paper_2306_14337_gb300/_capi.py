@@ -46,6 +46,7 @@ class Options(C.Structure):
         ("solve_ctas", C.c_int),
         ("update_map_budget", C.c_size_t),
         ("trace", C.c_int),
+        ("poll_ns_max", C.c_int),
         ("unpublished_row", C.c_int),
     ]
 

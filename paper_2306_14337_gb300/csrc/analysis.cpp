@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <atomic>
+#include <thread>
 
 namespace kkt {
 
@@ -490,7 +492,8 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
         }
     }
 
-    // update maps: one uint16 per multiply-add of the refactorization
+    // update maps: one uint16 per multiply-add of the refactorization; rows
+    // are independent, so they are filled in parallel after a prefix sum
     a.upd_off.clear();
     a.upd_map.clear();
     {
@@ -502,26 +505,49 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
         const bool fits = a.max_row <= 65535 && entries < 4.0e9 &&
                           entries * 2.0 + 4.0 * (double)nnz <= (double)map_budget_bytes;
         if (fits) {
-            a.upd_off.assign(nnz, 0);
-            a.upd_map.resize((size_t)entries);
-            size_t q = 0;
+            std::vector<long long> rowq(n + 1, 0);
             for (int i = 0; i < n; i++) {
-                const int rb = a.lu_rp[i], re = a.lu_rp[i + 1];
-                for (int t = rb; t < a.diag[i]; t++) {
+                long long c = 0;
+                for (int t = a.lu_rp[i]; t < a.diag[i]; t++) {
                     const int d = a.lu_ci[t];
-                    a.upd_off[t] = (unsigned)q;
-                    int w = t + 1;               // merge U(d, >d) into row i (both sorted)
-                    for (int u = a.diag[d] + 1; u < a.lu_rp[d + 1]; u++) {
-                        const int j = a.lu_ci[u];
-                        while (w < re && a.lu_ci[w] < j) w++;
-                        if (w >= re || a.lu_ci[w] != j) {
-                            err = "internal: update target outside the filled row";
-                            return A_ERR_ARG;
+                    c += a.lu_rp[d + 1] - a.diag[d] - 1;
+                }
+                rowq[i + 1] = rowq[i] + c;
+            }
+            a.upd_off.assign(nnz, 0);
+            a.upd_map.resize((size_t)rowq[n]);
+            std::atomic<int> bad{0};
+            auto fill = [&](int r0, int r1) {
+                for (int i = r0; i < r1; i++) {
+                    const int rb = a.lu_rp[i], re = a.lu_rp[i + 1];
+                    size_t q = (size_t)rowq[i];
+                    for (int t = rb; t < a.diag[i]; t++) {
+                        const int d = a.lu_ci[t];
+                        a.upd_off[t] = (unsigned)q;
+                        int w = t + 1;               // merge U(d, >d) into row i (both sorted)
+                        for (int u = a.diag[d] + 1; u < a.lu_rp[d + 1]; u++) {
+                            const int j = a.lu_ci[u];
+                            while (w < re && a.lu_ci[w] < j) w++;
+                            if (w >= re || a.lu_ci[w] != j) { bad = 1; return; }
+                            a.upd_map[q++] = (unsigned short)(w - rb);
                         }
-                        a.upd_map[q++] = (unsigned short)(w - rb);
                     }
                 }
+            };
+            unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+            if (rowq[n] < (1LL << 22)) nth = 1;
+            std::vector<std::thread> th;
+            int r0 = 0;
+            for (unsigned k = 0; k < nth; k++) {
+                const long long target = rowq[n] * (long long)(k + 1) / nth;
+                int r1 = r0;
+                while (r1 < n && (k + 1 == nth || rowq[r1] < target)) r1++;
+                if (k + 1 == nth) r1 = n;
+                th.emplace_back(fill, r0, r1);
+                r0 = r1;
             }
+            for (auto &t : th) t.join();
+            if (bad) { err = "internal: update target outside the filled row"; return A_ERR_ARG; }
         }
     }
     return A_OK;

@@ -65,6 +65,7 @@ struct RunCfg {
     unsigned long long *trace;   // optional: per work item {claim, done} %globaltimer (ns)
     long long trace_stride;      // words per phase region
     int unpublished_row;         // failure-detection test: this row is never published (-1: none)
+    unsigned poll_ns_max;        // backoff cap of a waiting lane (ns)
 };
 
 // Trace regions, one per phase, each (max work items) x 2 words.

@@ -203,7 +203,7 @@ template <typename T> __device__ __forceinline__ T wait_value(const RunCfg &rc, 
 
 // Warp-cooperative wait: every lane with need != 0 loads *p once; while some
 // lane still sees the marker, only the lowest such lane polls (exponential
-// backoff from 32 ns to 1 us), then the others reload once.  This keeps the
+// backoff from 32 ns up to poll_ns_max), then the others reload once.  This keeps the
 // polling traffic of thousands of waiting warps off the L2 that the critical
 // path needs.  Must be called by all 32 lanes.
 template <typename T>
@@ -220,7 +220,7 @@ __device__ __forceinline__ T warp_wait_load(const RunCfg &rc, const T *p, bool n
                 __nanosleep(ns);
                 v = ld_relaxed_v(p);
                 if (!is_marker(v)) break;
-                if (ns < 1024) ns <<= 1;
+                if (ns < rc.poll_ns_max) ns <<= 1;
                 if ((++it & 7) == 0) {
                     if (ld_relaxed(rc.status + ST_ABORT)) { bad = 1; break; }
                     if (it > rc.spin_limit) {
@@ -320,58 +320,125 @@ k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const doubl
             w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + t]] * aval[k] : 0.0);
         }
         __syncwarp();
-        for (int t0 = 0; t0 < dp; t0 += 32) {
-            // metadata of steps t0 .. t0+31, one step per lane
-            int md = 0, mub = 0, mue = 0;
-            unsigned mmo = 0;
+        // Pivot steps are pipelined: while step t computes, the reciprocal
+        // pivot and the first 32 x UJ entries (targets, values) of step t+1 are
+        // already in flight; a value still unpublished is polled again.
+        constexpr int UJ = 4;
+        int md = 0, mub = 0, mue = 0;       // metadata of steps t0..t0+31, one per lane
+        unsigned mmo = 0;
+        auto load_meta = [&](int t0) {
+            md = mub = mue = 0;
+            mmo = 0;
             if (t0 + lane < dp) {
                 md = P.lu_ci[rb + t0 + lane];
                 mub = P.diag[md];
                 mue = P.lu_rp[md + 1];
                 if (mapped) mmo = P.upd_off[rb + t0 + lane];
             }
-            const int te = min(dp - t0, 32);
-            for (int k = 0; k < te; k++) {
-                const int t = t0 + k;
-                const int d = __shfl_sync(FULL, md, k);
-                const int ub = __shfl_sync(FULL, mub, k);
-                const int ue = __shfl_sync(FULL, mue, k);
-                const unsigned mo = __shfl_sync(FULL, mmo, k);
-                if (mapped && k + 1 < te) {
-                    const unsigned mo1 = __shfl_sync(FULL, mmo, k + 1);
-                    const int n1 = __shfl_sync(FULL, mue, k + 1) - __shfl_sync(FULL, mub, k + 1) - 1;
-                    prefetch_l1(P.upd_map + mo1, 2LL * n1, lane);
-                }
-                const T r = warp_wait_load(rc, rcp + d, lane == 0, lane);
-                const T l = w[t] * __shfl_sync(FULL, r, 0);
-                for (int u0 = ub + 1; u0 < ue; u0 += 32) {
-                    const int u = u0 + lane;
-                    const bool in = u < ue;
-                    int lo = -1;
-                    if (in) {
-                        if (mapped) {
-                            lo = P.upd_map[mo + (u - ub - 1)];
-                        } else {
-                            const int j = P.lu_ci[u];
-                            lo = t + 1;
-                            int hi = len;
-                            while (lo < hi) {
-                                const int mid = (lo + hi) >> 1;
-                                if (c[mid] < j) lo = mid + 1; else hi = mid;
-                            }
-                            if (!(lo < len && c[lo] == j)) {   // pattern not closed under fill
-                                atomicExch(rc.status + ST_INTERNAL, 1);
-                                lo = -1;
-                            }
-                        }
-                    }
-                    const T uv = warp_wait_load(rc, LU + (in ? u : ub), in, lane);
-                    if (lo >= 0) w[lo] -= l * uv;
-                }
-                __syncwarp();
-                if (lane == 0) w[t] = l;
-                (void)d;
+        };
+        auto target = [&](int t, int ub, unsigned mo, int u) -> int {
+            if (mapped) return P.upd_map[mo + (u - ub - 1)];
+            const int j = P.lu_ci[u];
+            int a_ = t + 1, b_ = len;
+            while (a_ < b_) {
+                const int mid = (a_ + b_) >> 1;
+                if (c[mid] < j) a_ = mid + 1; else b_ = mid;
             }
+            if (a_ < len && c[a_] == j) return a_;
+            atomicExch(rc.status + ST_INTERNAL, 1);       // pattern not closed under fill
+            return -1;
+        };
+        // prefetched state of the next step
+        T pr = T(0);
+        int plo[UJ];
+        T pu[UJ];
+        auto prefetch = [&](int t, int d, int ub, int ue, unsigned mo) {
+            pr = ld_relaxed_v(rcp + d);
+#pragma unroll
+            for (int q = 0; q < UJ; q++) {
+                const int u = ub + 1 + 32 * q + lane;
+                plo[q] = -1;
+                pu[q] = T(0);
+                if (u < ue) {
+                    plo[q] = target(t, ub, mo, u);
+                    pu[q] = ld_relaxed_v(LU + u);
+                }
+            }
+        };
+        if (dp > 0) {
+            load_meta(0);
+            prefetch(0, __shfl_sync(FULL, md, 0), __shfl_sync(FULL, mub, 0), __shfl_sync(FULL, mue, 0),
+                     __shfl_sync(FULL, mmo, 0));
+        }
+        for (int t = 0; t < dp; t++) {
+            const int k = t & 31;
+            const int d = __shfl_sync(FULL, md, k);
+            const int ub = __shfl_sync(FULL, mub, k);
+            const int ue = __shfl_sync(FULL, mue, k);
+            const unsigned mo = __shfl_sync(FULL, mmo, k);
+            T r = pr;
+            int lo[UJ];
+            T uv[UJ];
+#pragma unroll
+            for (int q = 0; q < UJ; q++) { lo[q] = plo[q]; uv[q] = pu[q]; }
+            // next step's loads go out now
+            if (t + 1 < dp) {
+                if (k == 31) load_meta(t + 1);
+                const int k1 = (t + 1) & 31;
+                prefetch(t + 1, __shfl_sync(FULL, md, k1), __shfl_sync(FULL, mub, k1),
+                         __shfl_sync(FULL, mue, k1), __shfl_sync(FULL, mmo, k1));
+            }
+            // this step: reciprocal pivot and first block, polled only if unpublished
+            if (__any_sync(FULL, lane == 0 && is_marker(r))) {
+                const T w0 = warp_wait_load(rc, rcp + d, lane == 0, lane);
+                if (lane == 0) r = w0;
+            }
+            const T l = w[t] * __shfl_sync(FULL, r, 0);
+            unsigned need = 0;
+#pragma unroll
+            for (int q = 0; q < UJ; q++)
+                if (lo[q] >= 0 && is_marker(uv[q])) need |= 1u << q;
+            if (__any_sync(FULL, need != 0)) {
+#pragma unroll
+                for (int q = 0; q < UJ; q++) {
+                    const bool nq = (need >> q) & 1u;
+                    const T v = warp_wait_load(rc, LU + (nq ? ub + 1 + 32 * q + lane : ub), nq, lane);
+                    if (nq) uv[q] = v;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < UJ; q++)
+                if (lo[q] >= 0) w[lo[q]] -= l * uv[q];
+            // remaining blocks of long pivot rows
+            for (int u0 = ub + 1 + 32 * UJ; u0 < ue; u0 += 32 * UJ) {
+                int bl[UJ];
+                T bv[UJ];
+                unsigned bneed = 0;
+#pragma unroll
+                for (int q = 0; q < UJ; q++) {
+                    const int u = u0 + 32 * q + lane;
+                    bl[q] = -1;
+                    bv[q] = T(0);
+                    if (u < ue) {
+                        bl[q] = target(t, ub, mo, u);
+                        bv[q] = ld_relaxed_v(LU + u);
+                        if (is_marker(bv[q])) bneed |= 1u << q;
+                    }
+                }
+                if (__any_sync(FULL, bneed != 0)) {
+#pragma unroll
+                    for (int q = 0; q < UJ; q++) {
+                        const bool nq = (bneed >> q) & 1u;
+                        const T v = warp_wait_load(rc, LU + (nq ? u0 + 32 * q + lane : ub), nq, lane);
+                        if (nq) bv[q] = v;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < UJ; q++)
+                    if (bl[q] >= 0) w[bl[q]] -= l * bv[q];
+            }
+            __syncwarp();
+            if (lane == 0) w[t] = l;
         }
         // pivot test in FP64 (perturb to sign(a_ii) tau and count)
         if (lane == 0) {
@@ -546,17 +613,39 @@ k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T
 #pragma unroll
             for (int j = 0; j < SJ; j++)
                 if (j < nj) acc += val[j] * v[j];
-            // rows longer than 32 x SJ slots: the tail, loaded directly
-            for (int t0 = tb + 32 * SJ; t0 < te; t0 += 32) {
-                const int t = t0 + lane;
-                const bool in = t < te;
-                int c = 0;
-                T a = T(0);
-                if (in) { c = P.lu_ci[t]; a = F[t]; }
-                const bool inside = in && (BACKWARD ? (c <= hi) : (c >= lo)) && c - lo < tk.cap;
-                T w = warp_wait_load(rc, yout + c, in && !inside, lane);
-                if (inside) w = loc[c - lo];
-                acc += a * w;
+            // rows longer than 32 x SJ slots: further blocks of 32 x SJ, every
+            // block's loads issued before any of its waits
+            for (int t0 = tb + 32 * SJ; t0 < te; t0 += 32 * SJ) {
+                int bc[SJ];
+                T bv[SJ], bx[SJ];
+                load_slots(P, F, t0, te, lane, bc, bv);
+                unsigned bneed = 0;
+#pragma unroll
+                for (int j = 0; j < SJ; j++) {
+                    bx[j] = T(0);
+                    const int c = bc[j];
+                    if (c >= 0) {
+                        const bool inside = BACKWARD ? (c <= hi) : (c >= lo);
+                        if (inside && c - lo < tk.cap) {
+                            bx[j] = loc[c - lo];
+                        } else {
+                            bx[j] = ld_relaxed_v(yout + c);
+                            if (is_marker(bx[j])) bneed |= 1u << j;
+                        }
+                    }
+                }
+                if (__any_sync(FULL, bneed != 0)) {
+#pragma unroll
+                    for (int j = 0; j < SJ; j++) {
+                        const bool nq = (bneed >> j) & 1u;
+                        const T w = warp_wait_load(rc, yout + (nq ? bc[j] : 0), nq, lane);
+                        if (nq) bx[j] = w;
+                    }
+                }
+                const int bj = min(SJ, (te - t0 + 31) >> 5);
+#pragma unroll
+                for (int j = 0; j < SJ; j++)
+                    if (j < bj) acc += bv[j] * bx[j];
             }
             acc = warp_sum(acc);
             if (lane == kl) {
@@ -741,7 +830,7 @@ __device__ __forceinline__ T warp_wait_acquire(const RunCfg &rc, const T *p, boo
                 __nanosleep(ns);
                 v = ld_relaxed_v(p);
                 if (!is_marker(v)) break;
-                if (ns < 1024) ns <<= 1;
+                if (ns < rc.poll_ns_max) ns <<= 1;
                 if ((++it & 7) == 0) {
                     if (ld_relaxed(rc.status + ST_ABORT)) { bad = 1; break; }
                     if (it > rc.spin_limit) {
@@ -1115,6 +1204,7 @@ void kkt_default_options(kkt_options *o) {
     o->update_map_budget = 0;
     o->trace = 0;
     o->unpublished_row = -1;
+    o->poll_ns_max = 0;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -1341,6 +1431,7 @@ static kkt_status upload(kkt_ctx *c) {
     }
     c->rc.spin_limit = c->opt.spin_limit;
     c->rc.unpublished_row = -1;
+    c->rc.poll_ns_max = c->opt.poll_ns_max > 0 ? (unsigned)c->opt.poll_ns_max : 128u;
     if (c->opt.unpublished_row >= 0 && c->opt.unpublished_row < n)
         c->rc.unpublished_row = a.internal_of[c->opt.unpublished_row];
     c->rc.status = c->d_status;
@@ -1402,9 +1493,19 @@ kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_
     std::string err;
     int rc;
     try {
-        const long long budget = c->opt.device < 0 ? 0
-                                 : (c->opt.update_map_budget > 0 ? (long long)c->opt.update_map_budget
-                                                                 : (1LL << 30));
+        long long budget = 0;
+        if (c->opt.device >= 0) {
+            if (c->opt.update_map_budget > 0) {
+                budget = (long long)c->opt.update_map_budget;
+            } else {                          // a quarter of the free device memory, at most 16 GiB
+                DeviceGuard g(c->opt.device);
+                size_t fr = 0, tot = 0;
+                if (g.ok && cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+                    budget = std::min<long long>((long long)(fr / 4), 16LL << 30);
+                else
+                    budget = 1LL << 30;
+            }
+        }
         rc = analyze(n, row_ptr, col_idx, c->opt.ordering, c->opt.user_perm, c->an, err, budget);
     } catch (const std::bad_alloc &) {
         g_last_error = "host allocation failed during analysis";
