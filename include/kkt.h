@@ -267,6 +267,34 @@ kkt_status kkt_batch_refine_transpose(kkt_ctx *ctx, int B, const double *g_dev, 
 kkt_status kkt_batch_export_factors(kkt_ctx *ctx, int sys, double *out_dev, kkt_stream stream);
 
 /*
+ * Uneven batch: several contexts with different patterns (same device and
+ * factor precision) processed together.  Work items (system, row) and
+ * (system, task) are ordered by elimination level across systems and claimed
+ * from one device counter, so each phase (refactorization, forward and
+ * backward solve) is one persistent launch over all systems.
+ *
+ * kkt_queue_run: for every system k, refactor with values[k], solve into
+ * x[k] from b[k], then n_refine classic refinement steps; if omega_dev is not
+ * NULL (m doubles on the device) it receives each system's scaled residual.
+ * The whole sequence is recorded once into a CUDA graph and replayed; it is
+ * recorded again when any pointer or n_refine changes.  The arrays of
+ * pointers are host arrays of m device pointers.  The contexts keep the
+ * factors for later single-system calls.
+ * kkt_queue_solve_transpose: lam[k] = A_k^-T g[k] with the current factors.
+ * kkt_queue_set_launch: warps per CTA (1..8) and CTA count of the persistent
+ * kernels (0 = defaults), used by the autotuner.
+ */
+typedef struct kkt_queue kkt_queue;
+kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out);
+void kkt_queue_destroy(kkt_queue *q);
+kkt_status kkt_queue_set_launch(kkt_queue *q, int cta_warps, int ctas);
+kkt_status kkt_queue_run(kkt_queue *q, const double *const *values, const double *const *b,
+                         double *const *x, int n_refine, double *omega_dev, kkt_stream stream);
+kkt_status kkt_queue_solve_transpose(kkt_queue *q, const double *const *g, double *const *lam,
+                                     kkt_stream stream);
+kkt_status kkt_queue_status_sync(kkt_queue *q, kkt_stream stream, int *n_perturbed);
+
+/*
  * Scaled residual without any device allocation and without a context.
  *
  * The paper has no counterpart of this call; it exists for callers that cannot

@@ -4,6 +4,6 @@ The compute path is ``libkkt.so`` (hand-written CUDA for sm_103a behind the C
 interface in ``include/kkt.h``); this package only marshals arguments.
 """
 from ._capi import KKTError, load as load_library, lib_path
-from .solver import KKTSolver, kkt_solve
+from .solver import KKTQueue, KKTSolver, kkt_solve
 
-__all__ = ["KKTSolver", "kkt_solve", "KKTError", "load_library", "lib_path"]
+__all__ = ["KKTSolver", "KKTQueue", "kkt_solve", "KKTError", "load_library", "lib_path"]

@@ -118,6 +118,12 @@ SIGNATURES = {
     "kkt_batch_refine_transpose": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_double, C.c_int,
                                              C.POINTER(C.c_double), C.POINTER(C.c_int), _vp]),
     "kkt_batch_export_factors": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "kkt_queue_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
+    "kkt_queue_destroy": (None, [_vp]),
+    "kkt_queue_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "kkt_queue_run": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, _vp]),
+    "kkt_queue_solve_transpose": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), _vp]),
+    "kkt_queue_status_sync": (C.c_int, [_vp, _vp, _ip]),
     "kkt_scaled_residual_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -284,13 +285,184 @@ __device__ __forceinline__ void prefetch_l1(const void *p, long long bytes, int 
 // (one lane per step) and the next step's map segment is prefetched.  The
 // finished row is also written to the transposed layout (LUT[tpos[t]]) for
 // the transposed solves.
+// One row of the refactorization (the warp of lane `lane`); sval / scol are
+// the warp's shared-memory row of capacity rc.cap, gw its global warp index.
+template <typename T>
+__device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &rc,
+                                             const double *__restrict__ aval, const double *__restrict__ sp,
+                                             T *LU, T *LUT, T *rcp, double tau, int i, T *sval, int *scol,
+                                             int gw, int lane) {
+    const bool mapped = P.upd_off != nullptr;
+            const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
+            const int *c = P.lu_ci + rb;
+            T *w;
+            if (len <= rc.cap) {
+                w = sval;
+                if (!mapped) {
+                    for (int t = lane; t < len; t += 32) scol[t] = c[t];
+                    c = scol;
+                }
+            } else {
+                w = reinterpret_cast<T *>(rc.scratch) + (size_t)gw * rc.scratch_stride;
+            }
+            // gather A'(i,:) = s_i a_ij s_j into the row (structural zeros elsewhere)
+            const double si = sp[i];
+            for (int t = lane; t < len; t += 32) {
+                const int k = P.src[rb + t];
+                w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + t]] * aval[k] : 0.0);
+            }
+            __syncwarp();
+            // Pivot steps are pipelined: while step t computes, the reciprocal
+            // pivot and the first 32 x UJ entries (targets, values) of step t+1 are
+            // already in flight; a value still unpublished is polled again.
+            constexpr int UJ = 4;
+            int md = 0, mub = 0, mue = 0;       // metadata of steps t0..t0+31, one per lane
+            unsigned mmo = 0;
+            auto load_meta = [&](int t0) {
+                md = mub = mue = 0;
+                mmo = 0;
+                if (t0 + lane < dp) {
+                    md = P.lu_ci[rb + t0 + lane];
+                    mub = P.diag[md];
+                    mue = P.lu_rp[md + 1];
+                    if (mapped) mmo = P.upd_off[rb + t0 + lane];
+                }
+            };
+            auto target = [&](int t, int ub, unsigned mo, int u) -> int {
+                if (mapped) return P.upd_map[mo + (u - ub - 1)];
+                const int j = P.lu_ci[u];
+                int a_ = t + 1, b_ = len;
+                while (a_ < b_) {
+                    const int mid = (a_ + b_) >> 1;
+                    if (c[mid] < j) a_ = mid + 1; else b_ = mid;
+                }
+                if (a_ < len && c[a_] == j) return a_;
+                atomicExch(rc.status + ST_INTERNAL, 1);       // pattern not closed under fill
+                return -1;
+            };
+            // prefetched state of the next step
+            T pr = T(0);
+            int plo[UJ];
+            T pu[UJ];
+            auto prefetch = [&](int t, int d, int ub, int ue, unsigned mo) {
+                pr = ld_relaxed_v(rcp + d);
+    #pragma unroll
+                for (int q = 0; q < UJ; q++) {
+                    const int u = ub + 1 + 32 * q + lane;
+                    plo[q] = -1;
+                    pu[q] = T(0);
+                    if (u < ue) {
+                        plo[q] = target(t, ub, mo, u);
+                        pu[q] = ld_relaxed_v(LU + u);
+                    }
+                }
+            };
+            if (dp > 0) {
+                load_meta(0);
+                prefetch(0, __shfl_sync(FULL, md, 0), __shfl_sync(FULL, mub, 0), __shfl_sync(FULL, mue, 0),
+                         __shfl_sync(FULL, mmo, 0));
+            }
+            for (int t = 0; t < dp; t++) {
+                const int k = t & 31;
+                const int d = __shfl_sync(FULL, md, k);
+                const int ub = __shfl_sync(FULL, mub, k);
+                const int ue = __shfl_sync(FULL, mue, k);
+                const unsigned mo = __shfl_sync(FULL, mmo, k);
+                T r = pr;
+                int lo[UJ];
+                T uv[UJ];
+    #pragma unroll
+                for (int q = 0; q < UJ; q++) { lo[q] = plo[q]; uv[q] = pu[q]; }
+                // next step's loads go out now
+                if (t + 1 < dp) {
+                    if (k == 31) load_meta(t + 1);
+                    const int k1 = (t + 1) & 31;
+                    prefetch(t + 1, __shfl_sync(FULL, md, k1), __shfl_sync(FULL, mub, k1),
+                             __shfl_sync(FULL, mue, k1), __shfl_sync(FULL, mmo, k1));
+                }
+                // this step: reciprocal pivot and first block, polled only if unpublished
+                if (__any_sync(FULL, lane == 0 && is_marker(r))) {
+                    const T w0 = warp_wait_load(rc, rcp + d, lane == 0, lane);
+                    if (lane == 0) r = w0;
+                }
+                const T l = w[t] * __shfl_sync(FULL, r, 0);
+                unsigned need = 0;
+    #pragma unroll
+                for (int q = 0; q < UJ; q++)
+                    if (lo[q] >= 0 && is_marker(uv[q])) need |= 1u << q;
+                if (__any_sync(FULL, need != 0)) {
+    #pragma unroll
+                    for (int q = 0; q < UJ; q++) {
+                        const bool nq = (need >> q) & 1u;
+                        const T v = warp_wait_load(rc, LU + (nq ? ub + 1 + 32 * q + lane : ub), nq, lane);
+                        if (nq) uv[q] = v;
+                    }
+                }
+    #pragma unroll
+                for (int q = 0; q < UJ; q++)
+                    if (lo[q] >= 0) w[lo[q]] -= l * uv[q];
+                // remaining blocks of long pivot rows
+                for (int u0 = ub + 1 + 32 * UJ; u0 < ue; u0 += 32 * UJ) {
+                    int bl[UJ];
+                    T bv[UJ];
+                    unsigned bneed = 0;
+    #pragma unroll
+                    for (int q = 0; q < UJ; q++) {
+                        const int u = u0 + 32 * q + lane;
+                        bl[q] = -1;
+                        bv[q] = T(0);
+                        if (u < ue) {
+                            bl[q] = target(t, ub, mo, u);
+                            bv[q] = ld_relaxed_v(LU + u);
+                            if (is_marker(bv[q])) bneed |= 1u << q;
+                        }
+                    }
+                    if (__any_sync(FULL, bneed != 0)) {
+    #pragma unroll
+                        for (int q = 0; q < UJ; q++) {
+                            const bool nq = (bneed >> q) & 1u;
+                            const T v = warp_wait_load(rc, LU + (nq ? u0 + 32 * q + lane : ub), nq, lane);
+                            if (nq) bv[q] = v;
+                        }
+                    }
+    #pragma unroll
+                    for (int q = 0; q < UJ; q++)
+                        if (bl[q] >= 0) w[bl[q]] -= l * bv[q];
+                }
+                __syncwarp();
+                if (lane == 0) w[t] = l;
+            }
+            // pivot test in FP64 (perturb to sign(a_ii) tau and count)
+            if (lane == 0) {
+                double pv = (double)w[dp];
+                if (!(fabs(pv) >= tau) || isinf(pv)) {
+                    const int k = P.src[rb + dp];
+                    const double aii = (k >= 0) ? si * si * aval[k] : 0.0;
+                    if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
+                    pv = (aii < 0.0) ? -tau : tau;
+                    atomicAdd(rc.status + ST_PERTURBED, 1);
+                }
+                w[dp] = (T)pv;
+            }
+            __syncwarp();
+            // U part first (the signals of the rows below), then the reciprocal pivot
+            for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + rb + t, w[t]);
+            if (lane == 0) {
+                LU[rb + dp] = w[dp];
+                if (i != rc.unpublished_row) publish(rc, rcp + i, T(1) / w[dp]);
+            }
+            for (int t = lane; t < len; t += 32) {
+                if (t < dp) LU[rb + t] = w[t];
+                LUT[P.tpos[rb + t]] = w[t];
+            }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32, 2)
 k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const double *__restrict__ sp,
            T *LU, T *LUT, T *rcp, double tau_rel) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const bool mapped = P.upd_off != nullptr;
     T *sval = reinterpret_cast<T *>(smem) + (size_t)wid * rc.cap;
     int *scol = reinterpret_cast<int *>(smem + (size_t)nw * rc.cap * sizeof(T)) + (size_t)wid * rc.cap;
     const int e = rc.sched->epoch + 1;
@@ -300,169 +472,7 @@ k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const doubl
         const int slot = claim_row(rc, lane);
         if (slot >= P.n) break;
         trace_mark(rc, 0, slot, 0, lane);
-        const int i = P.order_f[slot];
-        const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
-        const int *c = P.lu_ci + rb;
-        T *w;
-        if (len <= rc.cap) {
-            w = sval;
-            if (!mapped) {
-                for (int t = lane; t < len; t += 32) scol[t] = c[t];
-                c = scol;
-            }
-        } else {
-            w = reinterpret_cast<T *>(rc.scratch) + (size_t)gw * rc.scratch_stride;
-        }
-        // gather A'(i,:) = s_i a_ij s_j into the row (structural zeros elsewhere)
-        const double si = sp[i];
-        for (int t = lane; t < len; t += 32) {
-            const int k = P.src[rb + t];
-            w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + t]] * aval[k] : 0.0);
-        }
-        __syncwarp();
-        // Pivot steps are pipelined: while step t computes, the reciprocal
-        // pivot and the first 32 x UJ entries (targets, values) of step t+1 are
-        // already in flight; a value still unpublished is polled again.
-        constexpr int UJ = 4;
-        int md = 0, mub = 0, mue = 0;       // metadata of steps t0..t0+31, one per lane
-        unsigned mmo = 0;
-        auto load_meta = [&](int t0) {
-            md = mub = mue = 0;
-            mmo = 0;
-            if (t0 + lane < dp) {
-                md = P.lu_ci[rb + t0 + lane];
-                mub = P.diag[md];
-                mue = P.lu_rp[md + 1];
-                if (mapped) mmo = P.upd_off[rb + t0 + lane];
-            }
-        };
-        auto target = [&](int t, int ub, unsigned mo, int u) -> int {
-            if (mapped) return P.upd_map[mo + (u - ub - 1)];
-            const int j = P.lu_ci[u];
-            int a_ = t + 1, b_ = len;
-            while (a_ < b_) {
-                const int mid = (a_ + b_) >> 1;
-                if (c[mid] < j) a_ = mid + 1; else b_ = mid;
-            }
-            if (a_ < len && c[a_] == j) return a_;
-            atomicExch(rc.status + ST_INTERNAL, 1);       // pattern not closed under fill
-            return -1;
-        };
-        // prefetched state of the next step
-        T pr = T(0);
-        int plo[UJ];
-        T pu[UJ];
-        auto prefetch = [&](int t, int d, int ub, int ue, unsigned mo) {
-            pr = ld_relaxed_v(rcp + d);
-#pragma unroll
-            for (int q = 0; q < UJ; q++) {
-                const int u = ub + 1 + 32 * q + lane;
-                plo[q] = -1;
-                pu[q] = T(0);
-                if (u < ue) {
-                    plo[q] = target(t, ub, mo, u);
-                    pu[q] = ld_relaxed_v(LU + u);
-                }
-            }
-        };
-        if (dp > 0) {
-            load_meta(0);
-            prefetch(0, __shfl_sync(FULL, md, 0), __shfl_sync(FULL, mub, 0), __shfl_sync(FULL, mue, 0),
-                     __shfl_sync(FULL, mmo, 0));
-        }
-        for (int t = 0; t < dp; t++) {
-            const int k = t & 31;
-            const int d = __shfl_sync(FULL, md, k);
-            const int ub = __shfl_sync(FULL, mub, k);
-            const int ue = __shfl_sync(FULL, mue, k);
-            const unsigned mo = __shfl_sync(FULL, mmo, k);
-            T r = pr;
-            int lo[UJ];
-            T uv[UJ];
-#pragma unroll
-            for (int q = 0; q < UJ; q++) { lo[q] = plo[q]; uv[q] = pu[q]; }
-            // next step's loads go out now
-            if (t + 1 < dp) {
-                if (k == 31) load_meta(t + 1);
-                const int k1 = (t + 1) & 31;
-                prefetch(t + 1, __shfl_sync(FULL, md, k1), __shfl_sync(FULL, mub, k1),
-                         __shfl_sync(FULL, mue, k1), __shfl_sync(FULL, mmo, k1));
-            }
-            // this step: reciprocal pivot and first block, polled only if unpublished
-            if (__any_sync(FULL, lane == 0 && is_marker(r))) {
-                const T w0 = warp_wait_load(rc, rcp + d, lane == 0, lane);
-                if (lane == 0) r = w0;
-            }
-            const T l = w[t] * __shfl_sync(FULL, r, 0);
-            unsigned need = 0;
-#pragma unroll
-            for (int q = 0; q < UJ; q++)
-                if (lo[q] >= 0 && is_marker(uv[q])) need |= 1u << q;
-            if (__any_sync(FULL, need != 0)) {
-#pragma unroll
-                for (int q = 0; q < UJ; q++) {
-                    const bool nq = (need >> q) & 1u;
-                    const T v = warp_wait_load(rc, LU + (nq ? ub + 1 + 32 * q + lane : ub), nq, lane);
-                    if (nq) uv[q] = v;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < UJ; q++)
-                if (lo[q] >= 0) w[lo[q]] -= l * uv[q];
-            // remaining blocks of long pivot rows
-            for (int u0 = ub + 1 + 32 * UJ; u0 < ue; u0 += 32 * UJ) {
-                int bl[UJ];
-                T bv[UJ];
-                unsigned bneed = 0;
-#pragma unroll
-                for (int q = 0; q < UJ; q++) {
-                    const int u = u0 + 32 * q + lane;
-                    bl[q] = -1;
-                    bv[q] = T(0);
-                    if (u < ue) {
-                        bl[q] = target(t, ub, mo, u);
-                        bv[q] = ld_relaxed_v(LU + u);
-                        if (is_marker(bv[q])) bneed |= 1u << q;
-                    }
-                }
-                if (__any_sync(FULL, bneed != 0)) {
-#pragma unroll
-                    for (int q = 0; q < UJ; q++) {
-                        const bool nq = (bneed >> q) & 1u;
-                        const T v = warp_wait_load(rc, LU + (nq ? u0 + 32 * q + lane : ub), nq, lane);
-                        if (nq) bv[q] = v;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < UJ; q++)
-                    if (bl[q] >= 0) w[bl[q]] -= l * bv[q];
-            }
-            __syncwarp();
-            if (lane == 0) w[t] = l;
-        }
-        // pivot test in FP64 (perturb to sign(a_ii) tau and count)
-        if (lane == 0) {
-            double pv = (double)w[dp];
-            if (!(fabs(pv) >= tau) || isinf(pv)) {
-                const int k = P.src[rb + dp];
-                const double aii = (k >= 0) ? si * si * aval[k] : 0.0;
-                if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
-                pv = (aii < 0.0) ? -tau : tau;
-                atomicAdd(rc.status + ST_PERTURBED, 1);
-            }
-            w[dp] = (T)pv;
-        }
-        __syncwarp();
-        // U part first (the signals of the rows below), then the reciprocal pivot
-        for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + rb + t, w[t]);
-        if (lane == 0) {
-            LU[rb + dp] = w[dp];
-            if (i != rc.unpublished_row) publish(rc, rcp + i, T(1) / w[dp]);
-        }
-        for (int t = lane; t < len; t += 32) {
-            if (t < dp) LU[rb + t] = w[t];
-            LUT[P.tpos[rb + t]] = w[t];
-        }
+        refactor_row<T>(P, rc, aval, sp, LU, LUT, rcp, tau, P.order_f[slot], sval, scol, gw, lane);
         trace_mark(rc, 0, slot, 1, lane);
     }
     if (lane == 0) finish_launch(rc, e);
@@ -511,6 +521,153 @@ __device__ __forceinline__ void load_slots(const DevPattern &P, const T *__restr
     }
 }
 
+// One task of a triangular solve (the warp of lane `lane`); loc is the warp's
+// shared-memory buffer of capacity tk.cap.
+template <typename T, bool BACKWARD, bool TRANS>
+__device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
+                                              const T *__restrict__ F, const T *__restrict__ rcp,
+                                              const double *__restrict__ rhs, const double *__restrict__ sp,
+                                              const T *__restrict__ yin, T *yout, double *__restrict__ out,
+                                              int accumulate, int tid, T *loc, int lane) {
+    constexpr bool DIV = (TRANS != BACKWARD);
+            const int lo = tk.task_lo[tid], hi = tk.task_hi[tid];
+            const int m = hi - lo + 1;
+            // row of walk step k, and its dependency slot range
+            auto row_of = [&](int k) { return BACKWARD ? hi - k : lo + k; };
+            auto meta = [&](int k, int &tb, int &te) {
+                const int i = row_of(k);
+                const int dg = P.diag[i];
+                tb = BACKWARD ? dg + 1 : P.lu_rp[i];
+                te = BACKWARD ? P.lu_rp[i + 1] : dg;
+            };
+            // per-lane metadata of the current and the next chunk of 32 steps
+            int ctb = 0, cte = 0, ntb = 0, nte = 0;
+            if (lane < m) meta(lane, ctb, cte);
+            if (32 + lane < m) meta(32 + lane, ntb, nte);
+            // owner data of this lane's step in the current chunk
+            T obase = T(0), orc = T(1);
+            double osp = 0.0, oold = 0.0;
+            int oo = 0;
+            auto owner = [&](int k) {
+                if (k >= m) return;
+                const int i = row_of(k);
+                if (DIV) orc = rcp[i];
+                if (BACKWARD) {
+                    obase = yin[i];
+                    osp = sp[i];
+                    oo = P.perm[i];
+                    if (accumulate) oold = out[oo];
+                } else {
+                    obase = (T)(sp[i] * rhs[P.perm[i]]);
+                }
+            };
+            owner(lane);
+            int ncol[SJ];
+            T nval[SJ];
+            load_slots(P, F, __shfl_sync(FULL, ctb, 0), __shfl_sync(FULL, cte, 0), lane, ncol, nval);
+            for (int k = 0; k < m; k++) {
+                const int kl = k & 31;
+                if (kl == 0 && k > 0) {                      // advance to the next chunk
+                    ctb = ntb; cte = nte;
+                    ntb = nte = 0;
+                    if (k + 32 + lane < m) meta(k + 32 + lane, ntb, nte);
+                    owner(k + lane);
+                }
+                const int i = row_of(k);
+                const int tb = __shfl_sync(FULL, ctb, kl), te = __shfl_sync(FULL, cte, kl);
+                int col[SJ];
+                T val[SJ], v[SJ];
+    #pragma unroll
+                for (int j = 0; j < SJ; j++) { col[j] = ncol[j]; val[j] = nval[j]; v[j] = T(0); }
+                if (k + 1 < m) {                             // next row's slots, in flight meanwhile
+                    const int src = (kl == 31) ? 0 : kl + 1;
+                    const int nb = (kl == 31) ? __shfl_sync(FULL, ntb, src) : __shfl_sync(FULL, ctb, src);
+                    const int ne = (kl == 31) ? __shfl_sync(FULL, nte, src) : __shfl_sync(FULL, cte, src);
+                    load_slots(P, F, nb, ne, lane, ncol, nval);
+                }
+                // dependency values: inside the task from shared memory, else polled
+                unsigned needm = 0;
+    #pragma unroll
+                for (int j = 0; j < SJ; j++) {
+                    const int c = col[j];
+                    if (c >= 0) {
+                        const bool inside = BACKWARD ? (c <= hi) : (c >= lo);
+                        if (inside && c - lo < tk.cap) {
+                            v[j] = loc[c - lo];
+                        } else {
+                            v[j] = ld_relaxed_v(yout + c);
+                            if (is_marker(v[j])) needm |= 1u << j;
+                        }
+                    }
+                }
+                if (__any_sync(FULL, needm != 0)) {
+    #pragma unroll
+                    for (int j = 0; j < SJ; j++) {
+                        const bool nj = (needm >> j) & 1u;
+                        const T w = warp_wait_load(rc, yout + (nj ? col[j] : 0), nj, lane);
+                        if (nj) v[j] = w;
+                    }
+                }
+                // FP64 instructions cost ~64 cycles each here: only the rounds the row needs
+                const int nj = min(SJ, (te - tb + 31) >> 5);
+                T acc = 0;
+    #pragma unroll
+                for (int j = 0; j < SJ; j++)
+                    if (j < nj) acc += val[j] * v[j];
+                // rows longer than 32 x SJ slots: further blocks of 32 x SJ, every
+                // block's loads issued before any of its waits
+                for (int t0 = tb + 32 * SJ; t0 < te; t0 += 32 * SJ) {
+                    int bc[SJ];
+                    T bv[SJ], bx[SJ];
+                    load_slots(P, F, t0, te, lane, bc, bv);
+                    unsigned bneed = 0;
+    #pragma unroll
+                    for (int j = 0; j < SJ; j++) {
+                        bx[j] = T(0);
+                        const int c = bc[j];
+                        if (c >= 0) {
+                            const bool inside = BACKWARD ? (c <= hi) : (c >= lo);
+                            if (inside && c - lo < tk.cap) {
+                                bx[j] = loc[c - lo];
+                            } else {
+                                bx[j] = ld_relaxed_v(yout + c);
+                                if (is_marker(bx[j])) bneed |= 1u << j;
+                            }
+                        }
+                    }
+                    if (__any_sync(FULL, bneed != 0)) {
+    #pragma unroll
+                        for (int j = 0; j < SJ; j++) {
+                            const bool nq = (bneed >> j) & 1u;
+                            const T w = warp_wait_load(rc, yout + (nq ? bc[j] : 0), nq, lane);
+                            if (nq) bx[j] = w;
+                        }
+                    }
+                    const int bj = min(SJ, (te - t0 + 31) >> 5);
+    #pragma unroll
+                    for (int j = 0; j < SJ; j++)
+                        if (j < bj) acc += bv[j] * bx[j];
+                }
+                acc = warp_sum(acc);
+                if (lane == kl) {
+                    T r = obase - acc;
+                    if (DIV) r = r * orc;
+                    if (is_marker(r)) {
+                        r = T(NAN);
+                        atomicExch(rc.status + ST_NONFINITE, 1);
+                    }
+                    const int p = i - lo;
+                    if (p < tk.cap) loc[p] = r;
+                    st_relaxed_v(yout + i, r);
+                    if (BACKWARD) {
+                        const double w = osp * (double)r;
+                        out[oo] = accumulate ? oold + w : w;
+                    }
+                }
+                __syncwarp();
+            }
+}
+
 template <typename T, bool BACKWARD, bool TRANS>
 __global__ void __launch_bounds__(WARPS * 32, 2)
 k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T *__restrict__ rcp,
@@ -521,150 +678,14 @@ k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T
     T *loc = reinterpret_cast<T *>(smem) + (size_t)wid * tk.cap;
     const int e = rc.sched->epoch + 1;
     const int *order = BACKWARD ? tk.order_b : tk.order_f;
-    constexpr bool DIV = (TRANS != BACKWARD);
     const long long tbase = (long long)rc.trace_stride * (TRANS ? (BACKWARD ? TR_TBWD : TR_TFWD)
                                                                 : (BACKWARD ? TR_BWD : TR_FWD));
     for (;;) {
         const int slot = claim_row(rc, lane);
         if (slot >= tk.ntasks) break;
         trace_mark(rc, tbase, slot, 0, lane);
-        const int tid = order[slot];
-        const int lo = tk.task_lo[tid], hi = tk.task_hi[tid];
-        const int m = hi - lo + 1;
-        // row of walk step k, and its dependency slot range
-        auto row_of = [&](int k) { return BACKWARD ? hi - k : lo + k; };
-        auto meta = [&](int k, int &tb, int &te) {
-            const int i = row_of(k);
-            const int dg = P.diag[i];
-            tb = BACKWARD ? dg + 1 : P.lu_rp[i];
-            te = BACKWARD ? P.lu_rp[i + 1] : dg;
-        };
-        // per-lane metadata of the current and the next chunk of 32 steps
-        int ctb = 0, cte = 0, ntb = 0, nte = 0;
-        if (lane < m) meta(lane, ctb, cte);
-        if (32 + lane < m) meta(32 + lane, ntb, nte);
-        // owner data of this lane's step in the current chunk
-        T obase = T(0), orc = T(1);
-        double osp = 0.0, oold = 0.0;
-        int oo = 0;
-        auto owner = [&](int k) {
-            if (k >= m) return;
-            const int i = row_of(k);
-            if (DIV) orc = rcp[i];
-            if (BACKWARD) {
-                obase = yin[i];
-                osp = sp[i];
-                oo = P.perm[i];
-                if (accumulate) oold = out[oo];
-            } else {
-                obase = (T)(sp[i] * rhs[P.perm[i]]);
-            }
-        };
-        owner(lane);
-        int ncol[SJ];
-        T nval[SJ];
-        load_slots(P, F, __shfl_sync(FULL, ctb, 0), __shfl_sync(FULL, cte, 0), lane, ncol, nval);
-        for (int k = 0; k < m; k++) {
-            const int kl = k & 31;
-            if (kl == 0 && k > 0) {                      // advance to the next chunk
-                ctb = ntb; cte = nte;
-                ntb = nte = 0;
-                if (k + 32 + lane < m) meta(k + 32 + lane, ntb, nte);
-                owner(k + lane);
-            }
-            const int i = row_of(k);
-            const int tb = __shfl_sync(FULL, ctb, kl), te = __shfl_sync(FULL, cte, kl);
-            int col[SJ];
-            T val[SJ], v[SJ];
-#pragma unroll
-            for (int j = 0; j < SJ; j++) { col[j] = ncol[j]; val[j] = nval[j]; v[j] = T(0); }
-            if (k + 1 < m) {                             // next row's slots, in flight meanwhile
-                const int src = (kl == 31) ? 0 : kl + 1;
-                const int nb = (kl == 31) ? __shfl_sync(FULL, ntb, src) : __shfl_sync(FULL, ctb, src);
-                const int ne = (kl == 31) ? __shfl_sync(FULL, nte, src) : __shfl_sync(FULL, cte, src);
-                load_slots(P, F, nb, ne, lane, ncol, nval);
-            }
-            // dependency values: inside the task from shared memory, else polled
-            unsigned needm = 0;
-#pragma unroll
-            for (int j = 0; j < SJ; j++) {
-                const int c = col[j];
-                if (c >= 0) {
-                    const bool inside = BACKWARD ? (c <= hi) : (c >= lo);
-                    if (inside && c - lo < tk.cap) {
-                        v[j] = loc[c - lo];
-                    } else {
-                        v[j] = ld_relaxed_v(yout + c);
-                        if (is_marker(v[j])) needm |= 1u << j;
-                    }
-                }
-            }
-            if (__any_sync(FULL, needm != 0)) {
-#pragma unroll
-                for (int j = 0; j < SJ; j++) {
-                    const bool nj = (needm >> j) & 1u;
-                    const T w = warp_wait_load(rc, yout + (nj ? col[j] : 0), nj, lane);
-                    if (nj) v[j] = w;
-                }
-            }
-            // FP64 instructions cost ~64 cycles each here: only the rounds the row needs
-            const int nj = min(SJ, (te - tb + 31) >> 5);
-            T acc = 0;
-#pragma unroll
-            for (int j = 0; j < SJ; j++)
-                if (j < nj) acc += val[j] * v[j];
-            // rows longer than 32 x SJ slots: further blocks of 32 x SJ, every
-            // block's loads issued before any of its waits
-            for (int t0 = tb + 32 * SJ; t0 < te; t0 += 32 * SJ) {
-                int bc[SJ];
-                T bv[SJ], bx[SJ];
-                load_slots(P, F, t0, te, lane, bc, bv);
-                unsigned bneed = 0;
-#pragma unroll
-                for (int j = 0; j < SJ; j++) {
-                    bx[j] = T(0);
-                    const int c = bc[j];
-                    if (c >= 0) {
-                        const bool inside = BACKWARD ? (c <= hi) : (c >= lo);
-                        if (inside && c - lo < tk.cap) {
-                            bx[j] = loc[c - lo];
-                        } else {
-                            bx[j] = ld_relaxed_v(yout + c);
-                            if (is_marker(bx[j])) bneed |= 1u << j;
-                        }
-                    }
-                }
-                if (__any_sync(FULL, bneed != 0)) {
-#pragma unroll
-                    for (int j = 0; j < SJ; j++) {
-                        const bool nq = (bneed >> j) & 1u;
-                        const T w = warp_wait_load(rc, yout + (nq ? bc[j] : 0), nq, lane);
-                        if (nq) bx[j] = w;
-                    }
-                }
-                const int bj = min(SJ, (te - t0 + 31) >> 5);
-#pragma unroll
-                for (int j = 0; j < SJ; j++)
-                    if (j < bj) acc += bv[j] * bx[j];
-            }
-            acc = warp_sum(acc);
-            if (lane == kl) {
-                T r = obase - acc;
-                if (DIV) r = r * orc;
-                if (is_marker(r)) {
-                    r = T(NAN);
-                    atomicExch(rc.status + ST_NONFINITE, 1);
-                }
-                const int p = i - lo;
-                if (p < tk.cap) loc[p] = r;
-                st_relaxed_v(yout + i, r);
-                if (BACKWARD) {
-                    const double w = osp * (double)r;
-                    out[oo] = accumulate ? oold + w : w;
-                }
-            }
-            __syncwarp();
-        }
+        trisolve_task<T, BACKWARD, TRANS>(P, rc, tk, F, rcp, rhs, sp, yin, yout, out, accumulate,
+                                          order[slot], loc, lane);
         trace_mark(rc, tbase, slot, 1, lane);
     }
     if (lane == 0) finish_launch(rc, e);
@@ -1048,6 +1069,87 @@ k_btrisolve(DevPattern P, RunCfg rc, TaskCfg tk, int B, const T *__restrict__ F,
         }
     }
     if (lane == 0) finish_launch(rc, e);
+}
+
+// ===========================================================================
+// Uneven batch: several contexts (different patterns) in one persistent
+// launch per phase.  Work items are (system, row) or (system, task), ordered
+// by level across systems (a topological order of every system), claimed from
+// one counter; each item reads its system's structures from a table.
+
+struct QSys {
+    DevPattern P;
+    TaskCfg tk;
+    void *LU, *LUT, *rcp, *y;          // factor, transposed factor, reciprocal pivots, 2n work
+    const double *sp;                  // scaling in permuted order
+    const unsigned long long *norms;   // the context's norm words (NM_AMAX for tau)
+    const double *values, *b, *rho;    // matrix values, right-hand side, residual
+    double *x;                         // solution (assigned, then accumulated)
+    const double *g;                   // transposed right-hand side
+    double *lam;                       // transposed solution
+    double tau_rel;
+    int n;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(WARPS * 32, 2)
+k_qrefactor(const QSys *__restrict__ sys, const int2 *__restrict__ items, int nitems, RunCfg rc) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *sval = reinterpret_cast<T *>(smem) + (size_t)wid * rc.cap;
+    int *scol = reinterpret_cast<int *>(smem + (size_t)nw * rc.cap * sizeof(T)) + (size_t)wid * rc.cap;
+    const int e = rc.sched->epoch + 1;
+    const int gw = blockIdx.x * nw + wid;
+    for (;;) {
+        const int slot = claim_row(rc, lane);
+        if (slot >= nitems) break;
+        const int2 it = items[slot];
+        const QSys &q = sys[it.x];
+        const double tau = q.tau_rel * __longlong_as_double((long long)q.norms[NM_AMAX]);
+        refactor_row<T>(q.P, rc, q.values, q.sp, (T *)q.LU, (T *)q.LUT, (T *)q.rcp, tau, it.y, sval, scol,
+                        gw, lane);
+    }
+    if (lane == 0) finish_launch(rc, e);
+}
+
+// phase: forward / backward; TRANS: transposed; refine: right-hand side is rho
+// and the solution is accumulated
+template <typename T, bool BACKWARD, bool TRANS>
+__global__ void __launch_bounds__(WARPS * 32, 2)
+k_qtrisolve(const QSys *__restrict__ sys, const int2 *__restrict__ items, int nitems, RunCfg rc, int refine,
+            int tcap) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int e = rc.sched->epoch + 1;
+    // per-warp slice of the queue-wide capacity (at least every system's tk.cap)
+    T *loc = reinterpret_cast<T *>(smem) + (size_t)wid * tcap;
+    for (;;) {
+        const int slot = claim_row(rc, lane);
+        if (slot >= nitems) break;
+        const int2 it = items[slot];
+        const QSys &q = sys[it.x];
+        T *y = (T *)q.y, *z = y + q.n;
+        const T *F = (const T *)(TRANS ? q.LUT : q.LU);
+        const double *rhs = TRANS ? q.g : (refine ? q.rho : q.b);
+        double *out = TRANS ? q.lam : q.x;
+        if (BACKWARD)
+            trisolve_task<T, true, TRANS>(q.P, rc, q.tk, F, (const T *)q.rcp, nullptr, q.sp, y, z, out,
+                                          TRANS ? 0 : refine, it.y, loc, lane);
+        else
+            trisolve_task<T, false, TRANS>(q.P, rc, q.tk, F, (const T *)q.rcp, rhs, q.sp, nullptr, y, nullptr, 0,
+                                           it.y, loc, lane);
+    }
+    if (lane == 0) finish_launch(rc, e);
+}
+
+// omega of one system from its norm words
+__global__ void k_omega(const unsigned long long *__restrict__ norms, double *__restrict__ out) {
+    const double an = __longlong_as_double((long long)norms[NM_ANORM]);
+    const double xm = __longlong_as_double((long long)norms[NM_XMAX]);
+    const double bm = __longlong_as_double((long long)norms[NM_BMAX]);
+    const double rm = __longlong_as_double((long long)norms[NM_RMAX]);
+    const double den = an * xm + bm;
+    *out = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
 }
 
 // rho = b - A x (or A^T x) per system, with per-system norms
@@ -2024,6 +2126,317 @@ kkt_status kkt_batch_export_factors(kkt_ctx *c, int sys, double *out_dev, kkt_st
                                                                      sys, out_dev, c->nnz_lu);
     CK(cudaGetLastError());
     c->launches++;
+    return KKT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// uneven-pattern queue
+
+struct kkt_queue {
+    std::vector<kkt_ctx *> ctx;
+    int m = 0, dev = -1;
+    bool f32 = false;
+    QSys *d_sys = nullptr;
+    std::vector<QSys> h_sys;
+    int2 *d_items = nullptr;          // refactor | forward | backward items
+    int n_ref = 0, n_fwd = 0, n_bwd = 0;
+    Sched *d_sched = nullptr;
+    int *d_status = nullptr;
+    void *d_scratch = nullptr;
+    RunCfg rc{};
+    int cta_warps = WARPS, grid = 0, sgrid = 0, cap = 32, tcap = 1;
+    size_t smem_ref = 0, smem_sol = 0;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void *> key;    // pointers and settings the captured graph was built with
+    long long launches = 0;
+};
+
+template <typename T> static kkt_status q_set_smem(kkt_queue *q) {
+    CK(cudaFuncSetAttribute(k_qrefactor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_ref));
+    CK(cudaFuncSetAttribute(k_qtrisolve<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_sol));
+    CK(cudaFuncSetAttribute(k_qtrisolve<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_sol));
+    CK(cudaFuncSetAttribute(k_qtrisolve<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_sol));
+    CK(cudaFuncSetAttribute(k_qtrisolve<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_sol));
+    return KKT_OK;
+}
+
+static kkt_status q_configure(kkt_queue *q, int cta_warps, int ctas) {
+    const size_t tsz = q->f32 ? sizeof(float) : sizeof(double);
+    q->cta_warps = std::max(1, std::min(cta_warps > 0 ? cta_warps : WARPS, WARPS));
+    const int nw = q->cta_warps;
+    q->smem_ref = (size_t)nw * q->cap * (tsz + sizeof(int));
+    q->smem_sol = (size_t)nw * q->tcap * tsz;
+    kkt_status st = q->f32 ? q_set_smem<float>(q) : q_set_smem<double>(q);
+    if (st) return st;
+    int sms = 0, per_sm = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, q->dev));
+    if (q->f32)
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qrefactor<float>, nw * 32, q->smem_ref));
+    else
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qrefactor<double>, nw * 32, q->smem_ref));
+    if (per_sm < 1) { g_last_error = "queue refactor kernel does not fit on an SM"; return KKT_ERR_CUDA; }
+    q->grid = ctas > 0 ? std::min(ctas, sms * per_sm) : sms * per_sm;
+    int per_sm_s = 0;
+    if (q->f32)
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_qtrisolve<float, false, false>, nw * 32, q->smem_sol));
+    else
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_qtrisolve<double, false, false>, nw * 32, q->smem_sol));
+    q->sgrid = ctas > 0 ? std::min(ctas, sms * std::max(per_sm_s, 1)) : sms * std::min(std::max(per_sm_s, 1), 2);
+    // scratch for rows longer than the shared-memory row
+    int longest = 0;
+    for (auto *c : q->ctx) if (c->an.max_row > q->cap) longest = std::max(longest, c->an.max_row);
+    cudaFree(q->d_scratch);
+    q->d_scratch = nullptr;
+    q->rc.scratch_stride = 0;
+    if (longest > 0) {
+        CK(cudaMalloc(&q->d_scratch, (size_t)longest * tsz * q->grid * nw));
+        q->rc.scratch_stride = longest;
+    }
+    q->rc.scratch = q->d_scratch;
+    q->rc.cap = q->cap;
+    if (q->graph) { cudaGraphExecDestroy(q->graph); q->graph = nullptr; }
+    q->key.clear();
+    return KKT_OK;
+}
+
+kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
+    if (!ctxs || m < 1 || !out) return KKT_ERR_ARG;
+    *out = nullptr;
+    std::unique_ptr<kkt_queue> q(new (std::nothrow) kkt_queue());
+    if (!q) return KKT_ERR_ALLOC;
+    q->m = m;
+    for (int k = 0; k < m; k++) {
+        kkt_ctx *c = ctxs[k];
+        if (!c || c->host_only) { g_last_error = "queue needs device contexts"; return KKT_ERR_ARG; }
+        if (k && (c->dev != ctxs[0]->dev || c->opt.factor_fp32 != ctxs[0]->opt.factor_fp32)) {
+            g_last_error = "queue contexts must share the device and the factor precision";
+            return KKT_ERR_ARG;
+        }
+        q->ctx.push_back(c);
+    }
+    q->dev = ctxs[0]->dev;
+    q->f32 = ctxs[0]->opt.factor_fp32 != 0;
+    DeviceGuard g(q->dev);
+    // items: refactor rows by (level, system, position); solve tasks by top level
+    std::vector<std::array<int, 4>> ref, fwd, bwd;
+    for (int k = 0; k < m; k++) {
+        const Analysis &a = q->ctx[k]->an;
+        for (int r = 0; r < a.n; r++) ref.push_back({a.level[a.order_f[r]], k, r, a.order_f[r]});
+        for (int t = 0; t < (int)a.task_lo.size(); t++) {
+            const int top = a.level[a.task_hi[t]];
+            fwd.push_back({top, k, t, t});
+            bwd.push_back({-top, k, t, t});
+        }
+        q->cap = std::max(q->cap, q->ctx[k]->cap);
+        q->tcap = std::max(q->tcap, q->ctx[k]->tk.cap);
+    }
+    std::sort(ref.begin(), ref.end());
+    std::sort(fwd.begin(), fwd.end());
+    std::sort(bwd.begin(), bwd.end());
+    std::vector<int2> items;
+    for (auto &v : ref) items.push_back(make_int2(v[1], v[3]));
+    for (auto &v : fwd) items.push_back(make_int2(v[1], v[3]));
+    for (auto &v : bwd) items.push_back(make_int2(v[1], v[3]));
+    q->n_ref = (int)ref.size();
+    q->n_fwd = (int)fwd.size();
+    q->n_bwd = (int)bwd.size();
+    CK(cudaMalloc(&q->d_items, items.size() * sizeof(int2)));
+    CK(cudaMemcpy(q->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&q->d_sys, m * sizeof(QSys)));
+    CK(cudaMalloc(&q->d_sched, sizeof(Sched)));
+    CK(cudaMemset(q->d_sched, 0, sizeof(Sched)));
+    CK(cudaMalloc(&q->d_status, ST_WORDS * sizeof(int)));
+    CK(cudaMemset(q->d_status, 0, ST_WORDS * sizeof(int)));
+    q->h_sys.resize(m);
+    for (int k = 0; k < m; k++) {
+        kkt_ctx *c = q->ctx[k];
+        QSys &s = q->h_sys[k];
+        std::memset(&s, 0, sizeof(s));
+        s.P = c->P;
+        s.tk = c->tk;
+        s.LU = c->d_lu;
+        s.LUT = c->d_lut;
+        s.rcp = c->d_rcp;
+        s.y = c->d_y;
+        s.sp = c->d_sp;
+        s.norms = c->d_norms;
+        s.rho = c->d_rho;
+        s.tau_rel = c->tau_rel;
+        s.n = c->an.n;
+    }
+    q->rc = ctxs[0]->rc;
+    q->rc.status = q->d_status;
+    q->rc.sched = q->d_sched;
+    q->rc.trace = nullptr;
+    q->rc.unpublished_row = -1;
+    kkt_status st = q_configure(q.get(), 0, 0);
+    if (st) { kkt_queue_destroy(q.release()); return st; }
+    *out = q.release();
+    return KKT_OK;
+}
+
+void kkt_queue_destroy(kkt_queue *q) {
+    if (!q) return;
+    DeviceGuard g(q->dev);
+    if (q->graph) cudaGraphExecDestroy(q->graph);
+    cudaFree(q->d_items);
+    cudaFree(q->d_sys);
+    cudaFree(q->d_sched);
+    cudaFree(q->d_status);
+    cudaFree(q->d_scratch);
+    delete q;
+}
+
+kkt_status kkt_queue_set_launch(kkt_queue *q, int cta_warps, int ctas) {
+    if (!q || cta_warps < 0 || ctas < 0) return KKT_ERR_ARG;
+    DeviceGuard g(q->dev);
+    return q_configure(q, cta_warps, ctas);
+}
+
+template <typename T>
+static kkt_status q_record(kkt_queue *q, int n_refine, double *omega_dev, cudaStream_t s) {
+    const int nw = q->cta_warps;
+    const int2 *ir = q->d_items, *iff = ir + q->n_ref, *ib = iff + q->n_fwd;
+    for (int k = 0; k < q->m; k++) {
+        kkt_ctx *c = q->ctx[k];
+        const QSys &h = q->h_sys[k];
+        const int n = c->an.n;
+        CK(cudaMemsetAsync(c->d_norms, 0, NM_WORDS * sizeof(unsigned long long), s));
+        k_scale<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, h.values, c->d_s, c->d_sp, c->d_norms, q->d_status,
+                                                         c->opt.equilibrate);
+        CK(cudaGetLastError());
+        k_amax<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, h.values, c->d_s, c->d_norms);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(c->d_lu, 0xff, (size_t)c->nnz_lu * sizeof(T), s));
+        CK(cudaMemsetAsync(c->d_rcp, 0xff, (size_t)n * sizeof(T), s));
+        q->launches += 2;
+    }
+    k_qrefactor<T><<<q->grid, nw * 32, q->smem_ref, s>>>(q->d_sys, ir, q->n_ref, q->rc);
+    CK(cudaGetLastError());
+    q->launches++;
+    for (int pass = 0; pass <= n_refine; pass++) {
+        if (pass > 0) {
+            for (int k = 0; k < q->m; k++) {
+                kkt_ctx *c = q->ctx[k];
+                const QSys &h = q->h_sys[k];
+                CK(cudaMemsetAsync(c->d_norms + NM_RMAX, 0, 3 * sizeof(unsigned long long), s));
+                k_resid<<<blocks_for(8LL * c->an.n, 256), 256, 0, s>>>(c->P, h.values, h.b, h.x, c->d_rho,
+                                                                      c->d_norms, 0);
+                CK(cudaGetLastError());
+                q->launches++;
+            }
+        }
+        for (int k = 0; k < q->m; k++)
+            CK(cudaMemsetAsync(q->ctx[k]->d_y, 0xff, 2 * (size_t)q->ctx[k]->an.n * sizeof(T), s));
+        k_qtrisolve<T, false, false><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, iff, q->n_fwd, q->rc, pass > 0, q->tcap);
+        CK(cudaGetLastError());
+        k_qtrisolve<T, true, false><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, ib, q->n_bwd, q->rc, pass > 0, q->tcap);
+        CK(cudaGetLastError());
+        q->launches += 2;
+    }
+    if (omega_dev) {
+        for (int k = 0; k < q->m; k++) {
+            kkt_ctx *c = q->ctx[k];
+            const QSys &h = q->h_sys[k];
+            CK(cudaMemsetAsync(c->d_norms + NM_RMAX, 0, 3 * sizeof(unsigned long long), s));
+            k_resid<<<blocks_for(8LL * c->an.n, 256), 256, 0, s>>>(c->P, h.values, h.b, h.x, c->d_rho, c->d_norms, 0);
+            CK(cudaGetLastError());
+            k_omega<<<1, 1, 0, s>>>(c->d_norms, omega_dev + k);
+            CK(cudaGetLastError());
+            q->launches += 2;
+        }
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_queue_run(kkt_queue *q, const double *const *values, const double *const *b, double *const *x,
+                         int n_refine, double *omega_dev, kkt_stream stream) {
+    if (!q || !values || !b || !x || n_refine < 0) return KKT_ERR_ARG;
+    DeviceGuard g(q->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<const void *> key;
+    for (int k = 0; k < q->m; k++) {
+        if (!values[k] || !b[k] || !x[k] || (const void *)b[k] == (const void *)x[k]) return KKT_ERR_ARG;
+        key.push_back(values[k]);
+        key.push_back(b[k]);
+        key.push_back(x[k]);
+    }
+    key.push_back((const void *)(intptr_t)n_refine);
+    key.push_back(omega_dev);
+    if (!q->graph || key != q->key) {
+        // new buffers or settings: refresh the system table and record the graph again
+        for (int k = 0; k < q->m; k++) {
+            q->h_sys[k].values = values[k];
+            q->h_sys[k].b = b[k];
+            q->h_sys[k].x = x[k];
+        }
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMemcpy(q->d_sys, q->h_sys.data(), q->m * sizeof(QSys), cudaMemcpyHostToDevice));
+        if (q->graph) { cudaGraphExecDestroy(q->graph); q->graph = nullptr; }
+        cudaStream_t cs;
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gr;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        kkt_status st = q->f32 ? q_record<float>(q, n_refine, omega_dev, cs) : q_record<double>(q, n_refine, omega_dev, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &gr);
+        cudaStreamDestroy(cs);
+        if (st) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&q->graph, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        q->key = key;
+        for (int k = 0; k < q->m; k++) {
+            q->ctx[k]->values = values[k];
+            q->ctx[k]->factored = true;
+        }
+    }
+    CK(cudaGraphLaunch(q->graph, s));
+    return KKT_OK;
+}
+
+kkt_status kkt_queue_solve_transpose(kkt_queue *q, const double *const *g_, double *const *lam, kkt_stream stream) {
+    if (!q || !g_ || !lam) return KKT_ERR_ARG;
+    DeviceGuard g(q->dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < q->m; k++) {
+        if (!g_[k] || !lam[k] || (const void *)g_[k] == (const void *)lam[k]) return KKT_ERR_ARG;
+        q->h_sys[k].g = g_[k];
+        q->h_sys[k].lam = lam[k];
+    }
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemcpy(q->d_sys, q->h_sys.data(), q->m * sizeof(QSys), cudaMemcpyHostToDevice));
+    const int nw = q->cta_warps;
+    const int2 *iff = q->d_items + q->n_ref, *ib = iff + q->n_fwd;
+    for (int k = 0; k < q->m; k++)
+        CK(cudaMemsetAsync(q->ctx[k]->d_y, 0xff, 2 * (size_t)q->ctx[k]->an.n *
+                                                  (q->f32 ? sizeof(float) : sizeof(double)), s));
+    if (q->f32) {
+        k_qtrisolve<float, false, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, iff, q->n_fwd, q->rc, 0, q->tcap);
+        CK(cudaGetLastError());
+        k_qtrisolve<float, true, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, ib, q->n_bwd, q->rc, 0, q->tcap);
+    } else {
+        k_qtrisolve<double, false, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, iff, q->n_fwd, q->rc, 0, q->tcap);
+        CK(cudaGetLastError());
+        k_qtrisolve<double, true, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, ib, q->n_bwd, q->rc, 0, q->tcap);
+    }
+    CK(cudaGetLastError());
+    q->launches += 2;
+    return KKT_OK;
+}
+
+kkt_status kkt_queue_status_sync(kkt_queue *q, kkt_stream stream, int *n_perturbed) {
+    if (!q) return KKT_ERR_ARG;
+    DeviceGuard g(q->dev);
+    int st[ST_WORDS];
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaMemcpy(st, q->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(q->d_status, 0, sizeof(st)));
+    if (n_perturbed) *n_perturbed = st[ST_PERTURBED];
+    if (st[ST_INTERNAL]) return KKT_ERR_INTERNAL;
+    if (st[ST_TIMEOUT]) return KKT_ERR_TIMEOUT;
+    if (st[ST_NONFINITE]) return KKT_ERR_NONFINITE;
+    if (st[ST_PERTURBED]) return KKT_WARN_PERTURBED;
     return KKT_OK;
 }
 

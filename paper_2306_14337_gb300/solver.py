@@ -275,3 +275,56 @@ def kkt_solve(solver: KKTSolver, values: torch.Tensor, b: torch.Tensor, tol: flo
               max_it: int = 20) -> torch.Tensor:
     """Differentiable x = A^-1 b for A given by ``values`` on the solver's pattern."""
     return _KKTSolveFn.apply(solver, values, b, tol, max_it)
+
+
+class KKTQueue:
+    """Several analysed patterns processed together: one persistent launch
+    per phase over all systems, recorded into a CUDA graph (kkt_queue_*)."""
+
+    def __init__(self, solvers):
+        self._lib = _capi.load()
+        self.solvers = list(solvers)
+        self.m = len(self.solvers)
+        arr = (C.c_void_p * self.m)(*[s_._h.value for s_ in self.solvers])
+        h = C.c_void_p()
+        check(self._lib.kkt_queue_create(arr, self.m, C.byref(h)), "kkt_queue_create")
+        self._h = h
+        self._keep = None
+        self.launch = (0, 0)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.kkt_queue_destroy(h)
+            self._h = None
+
+    def set_launch(self, cta_warps=0, ctas=0):
+        check(self._lib.kkt_queue_set_launch(self._h, int(cta_warps), int(ctas)), "kkt_queue_set_launch")
+        self.launch = (int(cta_warps), int(ctas))
+
+    @staticmethod
+    def _ptrs(ts):
+        return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def run(self, values, bs, xs, n_refine=2, omega=None, stream=None):
+        """values[k], bs[k], xs[k]: float64 CUDA tensors of system k."""
+        if not (len(values) == len(bs) == len(xs) == self.m):
+            raise ValueError("one tensor per system")
+        for k, sv in enumerate(self.solvers):
+            sv._vec(values[k], "values"); sv._vec(bs[k], "b"); sv._vec(xs[k], "x")
+        self._keep = (values, bs, xs, omega)
+        om = C.c_void_p(omega.data_ptr()) if omega is not None else C.c_void_p(0)
+        check(self._lib.kkt_queue_run(self._h, self._ptrs(values), self._ptrs(bs), self._ptrs(xs),
+                                      int(n_refine), om, _stream(stream)), "kkt_queue_run")
+        for k, sv in enumerate(self.solvers):
+            sv._values = values[k]
+
+    def solve_transpose(self, gs, lams, stream=None):
+        check(self._lib.kkt_queue_solve_transpose(self._h, self._ptrs(gs), self._ptrs(lams), _stream(stream)),
+              "kkt_queue_solve_transpose")
+
+    def status(self, stream=None):
+        k = C.c_int(0)
+        st = self._lib.kkt_queue_status_sync(self._h, _stream(stream), C.byref(k))
+        return st, k.value
+
