@@ -52,6 +52,14 @@ struct TaskCfg {
     const int *task_lo, *task_hi;        // rows of task t: [lo, hi], bottom to top
     const int *order_f, *order_b;        // claim orders of the forward / backward phases
     const int *order_topo;               // forward order without the longest-first prefix
+    // Long tasks of the single-system solves run on a whole CTA each: CTA b <
+    // nchain takes task chain_task[b]; the claim orders above then hold the
+    // other tasks only.  cs_late / cs_diag: per row of such a task, the slot
+    // splits of its dependency range by source block (see trisolve_chain).
+    int nchain;
+    int zcap;                            // results of a CTA task kept in shared memory
+    const int *chain_task;
+    const int *cs_late, *cs_diag;
 };
 
 struct RunCfg {

@@ -668,6 +668,198 @@ __device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg 
             }
 }
 
+// ---------------------------------------------------------------------------
+// Long tasks: one CTA per task.
+//
+// The steps of task [lo, hi] (bottom-up for the forward phases, top-down for
+// the backward ones) are cut into blocks of CB = 32.  Row i at step k of block
+// b = k / 32 splits its dependency slots by where their sources lie:
+//   early : other tasks, or steps of this task before block b - 1;
+//   late  : steps of block b - 1;
+//   diag  : steps of block b (before k).
+// Columns grow with the step in the forward phases and shrink in the backward
+// ones, so the three groups are contiguous slot ranges; the analysis stores
+// their boundaries (cs_late: early | late, cs_diag: late | diag in the forward
+// phases; mirrored in the backward ones).
+//
+// Warp 0 (the walker) solves block b row after row: lane j owns row j of the
+// block, the result of lane s is broadcast and every lane applies the diag
+// entry of its row to it (and the late entry of its row in block b + 1, so the
+// late part of the next block is complete when this block is).  Warps 1..
+// (the helpers) meanwhile gather block b + 1: the right-hand side minus the
+// early part (a warp per row, external sources polled in global memory) and
+// the two 32 x 32 tiles of diag / late entries the walker reads next.  One
+// CTA barrier per block; the per-row hand-off is a shuffle instead of a
+// global-memory round trip, and the bulk of the dot products runs on the
+// helpers, off the chain of dependent steps.
+constexpr int CB = 32;
+constexpr int TS = CB + 1;
+
+constexpr int CHAIN_MIN = 64;     // shortest task given a CTA
+constexpr int ZCAP_MAX = 8192;    // results of a CTA task kept in shared memory
+
+__host__ __device__ constexpr size_t chain_smem_words(int zcap) {
+    return (size_t)4 * CB * TS + 2 * CB + (size_t)zcap;
+}
+
+template <typename T, bool BACKWARD, bool TRANS>
+__device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
+                                               int lo, int hi, const T *__restrict__ F,
+                                               const T *__restrict__ rcp, const double *__restrict__ rhs,
+                                               const double *__restrict__ sp, const T *__restrict__ yin,
+                                               T *yout, double *__restrict__ out, int accumulate,
+                                               unsigned char *smem) {
+    constexpr bool DIV = (TRANS != BACKWARD);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m = hi - lo + 1, nb = (m + CB - 1) / CB;
+    T *td = reinterpret_cast<T *>(smem);       // [2][CB][TS]: diag entries of a block's rows
+    T *tl = td + 2 * CB * TS;                  // [2][CB][TS]: late entries of the next block's rows
+    T *xb = tl + 2 * CB * TS;                  // [2][CB]: right-hand side minus the early part
+    T *zs = xb + 2 * CB;                       // [zcap]: results of this task by step
+    const int zcap = tk.zcap;
+    auto row_of = [&](int k) { return BACKWARD ? hi - k : lo + k; };
+    auto step_of = [&](int c) { return BACKWARD ? hi - c : c - lo; };
+    // value of source column c (a step of this task before the current block,
+    // or another task's published result)
+    auto source = [&](int c, bool &pending) -> T {
+        pending = false;
+        if (c >= lo && c <= hi) {
+            const int st = step_of(c);
+            return st < zcap ? zs[st] : yout[c];
+        }
+        const T v = ld_relaxed_v(yout + c);
+        pending = is_marker(v);
+        return v;
+    };
+    // the three slot ranges of row i (forward: [tb, e) early, [e, d) late,
+    // [d, te) diag; backward: [tb, d) diag, [d, e) late, [e, te) early)
+    auto ranges = [&](int i, int &tb, int &e, int &d, int &te) {
+        const int dg = P.diag[i];
+        tb = BACKWARD ? dg + 1 : P.lu_rp[i];
+        te = BACKWARD ? P.lu_rp[i + 1] : dg;
+        e = tk.cs_late[i];
+        d = tk.cs_diag[i];
+    };
+
+    // helpers: prepare block B (x - early, diag tile) and the late tile of block B + 1
+    auto prepare = [&](int B) {
+        if (wid == 0 || B >= nb) return;
+        const int nh = nw - 1, h = wid - 1;
+        T *tdb = td + (B & 1) * CB * TS, *tlb = tl + (B & 1) * CB * TS, *xbb = xb + (B & 1) * CB;
+        const int k0 = B * CB, cnt = min(CB, m - k0);
+        for (int j = h; j < cnt; j += nh) {
+            const int i = row_of(k0 + j);
+            int tb, e, d, te;
+            ranges(i, tb, e, d, te);
+            // diag tile row j
+            for (int s = lane; s < TS; s += 32) tdb[j * TS + s] = T(0);
+            __syncwarp();
+            const int db = BACKWARD ? tb : d, de = BACKWARD ? d : te;
+            for (int t = db + lane; t < de; t += 32) tdb[j * TS + step_of(P.lu_ci[t]) - k0] = F[t];
+            // early part: a dot product over [eb, ee)
+            const int eb = BACKWARD ? e : tb, ee = BACKWARD ? te : e;
+            T acc = T(0);
+            for (int t0 = eb; t0 < ee; t0 += 32 * 4) {
+                int cc[4];
+                T fv[4], v[4];
+                unsigned need = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const int t = t0 + 32 * q + lane;
+                    cc[q] = -1;
+                    fv[q] = T(0);
+                    v[q] = T(0);
+                    if (t < ee) {
+                        cc[q] = P.lu_ci[t];
+                        fv[q] = F[t];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (cc[q] >= 0) {
+                        bool pend;
+                        v[q] = source(cc[q], pend);
+                        if (pend) need |= 1u << q;
+                    }
+                }
+                if (__any_sync(FULL, need != 0)) {
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const bool nq = (need >> q) & 1u;
+                        const T w = warp_wait_load(rc, yout + (nq ? cc[q] : 0), nq, lane);
+                        if (nq) v[q] = w;
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) acc += fv[q] * v[q];
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                const T base = BACKWARD ? yin[i] : (T)(sp[i] * rhs[P.perm[i]]);
+                xbb[j] = base - acc;
+            }
+        }
+        // late tile of block B + 1 (sources in block B)
+        if (B + 1 < nb) {
+            const int k1 = k0 + CB, cnt1 = min(CB, m - k1);
+            for (int j = h; j < cnt1; j += nh) {
+                const int i = row_of(k1 + j);
+                int tb, e, d, te;
+                ranges(i, tb, e, d, te);
+                for (int s = lane; s < TS; s += 32) tlb[j * TS + s] = T(0);
+                __syncwarp();
+                const int lb = BACKWARD ? d : e, le = BACKWARD ? e : d;
+                for (int t = lb + lane; t < le; t += 32) tlb[j * TS + step_of(P.lu_ci[t]) - k0] = F[t];
+            }
+        }
+    };
+
+    prepare(0);
+    __syncthreads();
+    T late = T(0);                              // walker: minus the late part of the next block's row
+    for (int b = 0; b < nb; b++) {
+        if (wid == 0) {
+            const T *tdb = td + (b & 1) * CB * TS + lane * TS;
+            const T *tlb = tl + (b & 1) * CB * TS + lane * TS;
+            const int k0 = b * CB, cnt = min(CB, m - k0);
+            const bool own = lane < cnt;
+            const int i = own ? row_of(k0 + lane) : row_of(k0);
+            T orc = T(1);
+            if (DIV && own) orc = rcp[i];
+            T acc = own ? xb[(b & 1) * CB + lane] + late : T(0);
+            late = T(0);
+            T z = T(0);
+#pragma unroll
+            for (int s = 0; s < CB; s++) {
+                if (s < cnt) {
+                    T zl = DIV ? acc * orc : acc;
+                    const T zb = __shfl_sync(FULL, zl, s);
+                    if (lane == s) z = zl;
+                    acc = fma(-tdb[s], zb, acc);
+                    late = fma(-tlb[s], zb, late);
+                }
+            }
+            if (own) {
+                if (is_marker(z)) {
+                    z = T(NAN);
+                    atomicExch(rc.status + ST_NONFINITE, 1);
+                }
+                const int k = k0 + lane;
+                if (k < zcap) zs[k] = z;
+                st_relaxed_v(yout + i, z);
+                if (BACKWARD) {
+                    const int oo = P.perm[i];
+                    const double w = sp[i] * (double)z;
+                    out[oo] = accumulate ? out[oo] + w : w;
+                }
+            }
+        } else {
+            prepare(b + 1);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, bool BACKWARD, bool TRANS>
 __global__ void __launch_bounds__(WARPS * 32, 2)
 k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T *__restrict__ rcp,
@@ -675,11 +867,21 @@ k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T
            T *yout, double *__restrict__ out, int accumulate) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    T *loc = reinterpret_cast<T *>(smem) + (size_t)wid * tk.cap;
     const int e = rc.sched->epoch + 1;
-    const int *order = BACKWARD ? tk.order_b : tk.order_f;
     const long long tbase = (long long)rc.trace_stride * (TRANS ? (BACKWARD ? TR_TBWD : TR_TFWD)
                                                                 : (BACKWARD ? TR_BWD : TR_FWD));
+    if ((int)blockIdx.x < tk.nchain) {            // a long task on this whole CTA
+        const int tid = tk.chain_task[blockIdx.x];
+        const int item = tk.ntasks + blockIdx.x;
+        if (wid == 0) trace_mark(rc, tbase, item, 0, lane);
+        trisolve_chain<T, BACKWARD, TRANS>(P, rc, tk, tk.task_lo[tid], tk.task_hi[tid], F, rcp, rhs, sp,
+                                           yin, yout, out, accumulate, smem);
+        if (wid == 0) trace_mark(rc, tbase, item, 1, lane);
+        if (lane == 0) finish_launch(rc, e);
+        return;
+    }
+    T *loc = reinterpret_cast<T *>(smem) + (size_t)wid * tk.cap;
+    const int *order = BACKWARD ? tk.order_b : tk.order_f;
     for (;;) {
         const int slot = claim_row(rc, lane);
         if (slot >= tk.ntasks) break;
@@ -1239,7 +1441,9 @@ struct kkt_ctx {
     const double *b_values = nullptr;
     int b_factored = 0;
     int *d_view_slot = nullptr;
-    TaskCfg tk{};
+    TaskCfg tk{};             // all tasks (batched and queued solves)
+    TaskCfg tk1{};            // single-system solves: CTA tasks + warp tasks
+    const int *cs_fwd = nullptr, *csd_fwd = nullptr, *cs_bwd = nullptr, *csd_bwd = nullptr;
     size_t solve_smem = 0;
     unsigned long long *h_norms = nullptr;  // pinned
     int grid = 0, solve_grid = 0, cta_warps = WARPS, cap = 0;
@@ -1438,14 +1642,15 @@ static kkt_status upload(kkt_ctx *c) {
             len[T] = a.task_hi[T] - a.task_lo[T] + 1;
             top[T] = a.level[a.task_hi[T]];
         }
-        // the longest tasks (fewer than a quarter of the resident warps) first
-        const long long warps = (long long)c->solve_grid * nw;
-        std::vector<int> bylen(nt);
-        std::iota(bylen.begin(), bylen.end(), 0);
-        std::sort(bylen.begin(), bylen.end(), [&](int x, int y) { return len[x] > len[y]; });
-        const long long max_long = std::max(0LL, warps / 4);
-        int lmin = INT32_MAX;
-        {
+        // Claim orders over a set of tasks: forward = the longest tasks (fewer
+        // than a quarter of the resident warps) first, then by level of the top
+        // row; backward = from the root; topological = by level only.
+        auto orders = [&](const std::vector<int> &set, long long warps, std::vector<int> &of,
+                          std::vector<int> &ob, std::vector<int> &ot) {
+            std::vector<int> bylen(set);
+            std::sort(bylen.begin(), bylen.end(), [&](int x, int y) { return len[x] > len[y]; });
+            const long long max_long = std::max(0LL, warps / 4);
+            int lmin = INT32_MAX;
             long long cnt = 0;
             size_t q = 0;
             while (q < bylen.size()) {
@@ -1456,45 +1661,137 @@ static kkt_status upload(kkt_ctx *c) {
                 lmin = len[bylen[q]];
                 q = r;
             }
+            of = set;
+            ob = set;
+            ot = set;
+            std::stable_sort(of.begin(), of.end(), [&](int x, int y) {
+                const bool lx = len[x] >= lmin, ly = len[y] >= lmin;
+                if (lx != ly) return lx;
+                return top[x] < top[y];
+            });
+            std::stable_sort(ob.begin(), ob.end(), [&](int x, int y) { return top[x] > top[y]; });
+            std::stable_sort(ot.begin(), ot.end(), [&](int x, int y) { return top[x] < top[y]; });
+        };
+        std::vector<int> all(nt);
+        std::iota(all.begin(), all.end(), 0);
+        std::vector<int> of, ob, ot;
+        orders(all, (long long)c->solve_grid * nw, of, ob, ot);
+        // Single-system solves: the longest tasks (at least CHAIN_MIN rows, at
+        // most a quarter of the CTAs) run on a CTA each; the rest are claimed
+        // by warps.
+        std::vector<int> chain, reg;
+        if (nw >= 4 && c->solve_grid >= 8) {
+            std::vector<int> bylen(all);
+            std::stable_sort(bylen.begin(), bylen.end(), [&](int x, int y) { return len[x] > len[y]; });
+            const int max_chain = c->solve_grid / 4;
+            for (int T : bylen) {
+                if ((int)chain.size() >= max_chain || len[T] < CHAIN_MIN) break;
+                chain.push_back(T);
+            }
         }
-        std::vector<int> of(nt), ob(nt);
-        std::iota(of.begin(), of.end(), 0);
-        std::iota(ob.begin(), ob.end(), 0);
-        std::stable_sort(of.begin(), of.end(), [&](int x, int y) {
-            const bool lx = len[x] >= lmin, ly = len[y] >= lmin;
-            if (lx != ly) return lx;
-            return top[x] < top[y];
-        });
-        std::stable_sort(ob.begin(), ob.end(), [&](int x, int y) { return top[x] > top[y]; });
-        std::vector<int> ot(nt);
-        std::iota(ot.begin(), ot.end(), 0);
-        std::stable_sort(ot.begin(), ot.end(), [&](int x, int y) { return top[x] < top[y]; });
+        {
+            std::vector<char> is_chain(nt, 0);
+            for (int T : chain) is_chain[T] = 1;
+            for (int T = 0; T < nt; T++)
+                if (!is_chain[T]) reg.push_back(T);
+        }
+        std::vector<int> of1, ob1, ot1;
+        orders(reg, (long long)(c->solve_grid - (int)chain.size()) * nw, of1, ob1, ot1);
+        // slot splits of the rows of CTA tasks (forward / backward phases share
+        // them: cs_late and cs_diag are column bounds turned into slots)
+        int zmax = 0;
+        for (int T : chain) zmax = std::max(zmax, len[T]);
+        // Forward and backward phases walk the task in opposite directions, so
+        // the splits differ; both are stored: [0, n) forward, [n, 2n) backward.
+        std::vector<int> csl(2 * (size_t)n, -1), csd(2 * (size_t)n, -1);
+        for (int T : chain) {
+            const int lo = a.task_lo[T], hi = a.task_hi[T];
+            for (int i = lo; i <= hi; i++) {
+                const int rb = a.lu_rp[i], dg = a.diag[i], re = a.lu_rp[i + 1];
+                const int *ci = a.lu_ci.data();
+                // forward: step k = i - lo, block b; sources with column >= lo + CB*max(b-1,0)
+                // are late or diag, >= lo + CB*b diag
+                {
+                    const int k = i - lo, b = k / CB;
+                    const int c_late = lo + CB * std::max(b - 1, 0), c_diag = lo + CB * b;
+                    csl[i] = (int)(std::lower_bound(ci + rb, ci + dg, c_late) - ci);
+                    csd[i] = (int)(std::lower_bound(ci + rb, ci + dg, c_diag) - ci);
+                }
+                // backward: step k = hi - i; sources with column <= hi - CB*max(b-1,0)
+                // are late or diag, <= hi - CB*b diag (a head of the U slots)
+                {
+                    const int k = hi - i, b = k / CB;
+                    const int c_late = hi - CB * std::max(b - 1, 0), c_diag = hi - CB * b;
+                    csl[n + (size_t)i] = (int)(std::upper_bound(ci + dg + 1, ci + re, c_late) - ci);
+                    csd[n + (size_t)i] = (int)(std::upper_bound(ci + dg + 1, ci + re, c_diag) - ci);
+                }
+            }
+        }
         int *d = nullptr;
-        CK(cudaMalloc(&d, 3 * (size_t)nt * sizeof(int)));
-        CK(cudaMemcpy(d, of.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(d + nt, ob.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(d + 2 * nt, ot.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+        const size_t words = 3 * (size_t)nt + 3 * (size_t)nt + chain.size() + 4 * (size_t)n;
+        CK(cudaMalloc(&d, words * sizeof(int)));
+        size_t o = 0;
+        auto put = [&](const std::vector<int> &v) -> const int * {
+            const int *p = d + o;
+            if (!v.empty()) {
+                cudaError_t e = cudaMemcpy(d + o, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice);
+                if (e != cudaSuccess) return nullptr;
+            }
+            o += v.size();
+            return p;
+        };
         c->d_task_orders = d;
         c->tk.ntasks = nt;
-        c->tk.order_f = d;
-        c->tk.order_b = d + nt;
-        c->tk.order_topo = d + 2 * nt;
+        c->tk.order_f = put(of);
+        c->tk.order_b = put(ob);
+        c->tk.order_topo = put(ot);
+        c->tk1.task_lo = c->tk.task_lo;
+        c->tk1.task_hi = c->tk.task_hi;
+        c->tk1.ntasks = (int)reg.size();
+        c->tk1.order_f = put(of1);
+        c->tk1.order_b = put(ob1);
+        c->tk1.order_topo = put(ot1);
+        c->tk1.nchain = (int)chain.size();
+        c->tk1.chain_task = put(chain);
+        c->cs_fwd = put(std::vector<int>(csl.begin(), csl.begin() + n));
+        c->cs_bwd = put(std::vector<int>(csl.begin() + n, csl.end()));
+        c->csd_fwd = put(std::vector<int>(csd.begin(), csd.begin() + n));
+        c->csd_bwd = put(std::vector<int>(csd.begin() + n, csd.end()));
+        if (!c->tk.order_f || !c->tk1.order_f || !c->tk1.chain_task || !c->cs_fwd || !c->csd_bwd) {
+            g_last_error = "copy of the task tables failed";
+            return KKT_ERR_CUDA;
+        }
         c->tk.cap = std::min(a.max_task, 1024);
-        c->solve_smem = (size_t)nw * c->tk.cap * tsz;
-        c->device_bytes += 2 * (size_t)nt * sizeof(int);
+        int max_reg = 1;
+        for (int T : reg) max_reg = std::max(max_reg, len[T]);
+        c->tk1.cap = std::min(max_reg, 1024);
+        c->tk1.zcap = std::min(zmax, ZCAP_MAX);
+        c->device_bytes += words * sizeof(int);
+        c->solve_smem = std::max((size_t)nw * c->tk1.cap * tsz,
+                                 c->tk1.nchain ? chain_smem_words(c->tk1.zcap) * tsz : 0);
         auto setsm = [&](const void *f) {
             return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->solve_smem);
         };
+        int per_sm_s = 0;
         if (f32) {
             CK(setsm((const void *)k_trisolve<float, false, false>));
             CK(setsm((const void *)k_trisolve<float, true, false>));
             CK(setsm((const void *)k_trisolve<float, false, true>));
             CK(setsm((const void *)k_trisolve<float, true, true>));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_trisolve<float, false, false>,
+                                                             nw * 32, c->solve_smem));
         } else {
             CK(setsm((const void *)k_trisolve<double, false, false>));
             CK(setsm((const void *)k_trisolve<double, true, false>));
             CK(setsm((const void *)k_trisolve<double, false, true>));
             CK(setsm((const void *)k_trisolve<double, true, true>));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_trisolve<double, false, false>,
+                                                             nw * 32, c->solve_smem));
+        }
+        // every CTA of a solve must be resident at once (CTA tasks and waiting warps)
+        if ((long long)per_sm_s * sms < c->solve_grid) {
+            g_last_error = "solve grid does not fit on the device at once";
+            return KKT_ERR_CUDA;
         }
     }
     if (c->opt.refine_mode == KKT_REFINE_FGMRES || c->opt.refine_mode == KKT_REFINE_AUTO) {
@@ -1653,6 +1950,15 @@ template <typename T> static kkt_status launch_refactor(kkt_ctx *c, cudaStream_t
     return KKT_OK;
 }
 
+// task configuration of a single-system solve phase (the slot splits of CTA
+// tasks depend on the direction of the walk)
+static TaskCfg tasks_of(const kkt_ctx *c, bool backward) {
+    TaskCfg t = c->tk1;
+    t.cs_late = backward ? c->cs_bwd : c->cs_fwd;
+    t.cs_diag = backward ? c->csd_bwd : c->csd_fwd;
+    return t;
+}
+
 template <typename T>
 static kkt_status launch_solve(kkt_ctx *c, const double *b, double *x, int accumulate, cudaStream_t s) {
     const int n = c->an.n;
@@ -1660,11 +1966,11 @@ static kkt_status launch_solve(kkt_ctx *c, const double *b, double *x, int accum
     const T *L = (const T *)c->d_lu, *R = (const T *)c->d_rcp;
     CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
     k_trisolve<T, false, false><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
-        c->P, c->rc, c->tk, L, R, b, c->d_sp, nullptr, y, nullptr, 0);
+        c->P, c->rc, tasks_of(c, false), L, R, b, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
     c->launches++;
     k_trisolve<T, true, false><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
-        c->P, c->rc, c->tk, L, R, nullptr, c->d_sp, y, z, x, accumulate);
+        c->P, c->rc, tasks_of(c, true), L, R, nullptr, c->d_sp, y, z, x, accumulate);
     CK(cudaGetLastError());
     c->launches++;
     return KKT_OK;
@@ -1678,11 +1984,11 @@ static kkt_status launch_solve_t(kkt_ctx *c, const double *g, double *lam, int a
     const T *L = (const T *)c->d_lut, *R = (const T *)c->d_rcp;
     CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
     k_trisolve<T, false, true><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
-        c->P, c->rc, c->tk, L, R, g, c->d_sp, nullptr, y, nullptr, 0);
+        c->P, c->rc, tasks_of(c, false), L, R, g, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
     c->launches++;
     k_trisolve<T, true, true><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
-        c->P, c->rc, c->tk, L, R, nullptr, c->d_sp, y, z, lam, accumulate);
+        c->P, c->rc, tasks_of(c, true), L, R, nullptr, c->d_sp, y, z, lam, accumulate);
     CK(cudaGetLastError());
     c->launches++;
     return KKT_OK;
