@@ -82,9 +82,11 @@ typedef struct {
     int device;             /* CUDA device ordinal; -1 = host-only analysis (no CUDA
                                call at all; only the kkt_get_* / export calls work) */
     int max_batch;          /* capacity of the batched calls, fixed at analysis */
-    int cta_warps;          /* warps per CTA of the persistent kernels (1..8; 0 = 8) */
+    int cta_warps;          /* warps per CTA of the persistent kernels (1..8; 0 = 8);
+                               the single-system triangular solves use twice as many */
     int refactor_ctas;      /* CTAs of the refactorization (0 = all that fit at once) */
-    int solve_ctas;         /* CTAs of the triangular solves (0 = 2 per SM) */
+    int solve_ctas;         /* CTAs of the single-system triangular solves (0 = one per
+                               SM); every CTA must fit on the device at once */
     size_t update_map_budget; /* bytes allowed for the refactorization's update maps
                                  (relative positions of every multiply-add; 0 = 1 GiB);
                                  over budget the kernel searches each row instead */
@@ -112,8 +114,8 @@ typedef struct {
     double bytes_spmv;      /* compulsory bytes of one residual */
     size_t device_bytes;    /* device memory held by the context */
     int grid_ctas;          /* CTAs of the refactorization */
-    int solve_ctas;         /* CTAs of the triangular solves */
-    int warps_per_cta;
+    int solve_ctas;         /* CTAs of the single-system triangular solves */
+    int warps_per_cta;      /* of the refactorization and the batched kernels */
     int last_refine_iters;  /* solves used by the last kkt_refine */
     double last_omega;      /* scaled residual after the last kkt_refine */
     int factor_fp32;

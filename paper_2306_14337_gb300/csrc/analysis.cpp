@@ -452,7 +452,16 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
         ord.resize(n);
         for (int i = 0; i < n; i++) ord[c[lev[i]]++] = i;
     };
-    by_level(a.level, a.n_levels, a.order_f);
+    // Refactorization claim order: deepest rows first (distance to the root,
+    // descending; Hu's critical-path-first list schedule for an in-tree).  A
+    // row depends only on its descendants, which are deeper, so the order is
+    // topological; unlike an order by height it starts the long paths of the
+    // tree first instead of every leaf of the tree.
+    {
+        std::vector<int> neg(n);
+        for (int i = 0; i < n; i++) neg[i] = a.n_levels_u - 1 - a.level_u[i];
+        by_level(neg, a.n_levels_u, a.order_f);
+    }
     by_level(a.level_u, a.n_levels_u, a.order_b);
 
     // flops of one refactorization: each pivot d eliminated from the rows of

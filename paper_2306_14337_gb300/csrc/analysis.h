@@ -34,8 +34,8 @@ struct Analysis {
     std::vector<int> tpos;         // slot of the transposed entry (diagonal: itself)
     // levels and schedules
     std::vector<int> level, level_u;
-    std::vector<int> order_f;      // rows by (level, index)
-    std::vector<int> order_b;      // rows by (level_u, index)
+    std::vector<int> order_f;      // rows by depth, deepest first (refactorization claim order)
+    std::vector<int> order_b;      // rows by depth, root first
     int n_levels = 0, n_levels_u = 0;
     long long nnz_sym = 0;
     int max_row = 0;

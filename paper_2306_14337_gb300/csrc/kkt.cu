@@ -7,7 +7,7 @@
 //          at the start of every row of k_refactor;
 //   Sec. 5.2 Algorithm 1 (row-wise, dependency-driven LU)
 //       -> k_refactor: one warp per row of the combined L+U (CSR), rows
-//          claimed in level order, ready flags on the rows it depends on,
+//          claimed deepest first, ready flags on the rows it depends on,
 //          the row staged in shared memory, updates placed by a binary search
 //          of the row's sorted column list (no atomics);
 //   Sec. 5.2 Algorithm 2 (dependency-driven triangular solve)
@@ -272,7 +272,7 @@ __device__ __forceinline__ void prefetch_l1(const void *p, long long bytes, int 
 
 // ---------------------------------------------------------------------------
 // numeric refactorization: one warp per row of L+U (Algorithm 1's row-wise
-// elimination, fixed pivots), rows claimed in level order.
+// elimination, fixed pivots), rows claimed deepest first (distance to the root).
 //
 // Row i is gathered (scaled) into shared memory; for every pivot row d < i in
 // L(i,:), in increasing d, the multiplier l = w[d] * (1 / U(d,d)) is formed
@@ -398,9 +398,11 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                         if (nq) uv[q] = v;
                     }
                 }
+                // rounds past the end of the pivot row are skipped as a whole
+                // (an FP64 instruction costs the same with idle lanes)
     #pragma unroll
                 for (int q = 0; q < UJ; q++)
-                    if (lo[q] >= 0) w[lo[q]] -= l * uv[q];
+                    if (32 * q < ue - ub - 1 && lo[q] >= 0) w[lo[q]] -= l * uv[q];
                 // remaining blocks of long pivot rows
                 for (int u0 = ub + 1 + 32 * UJ; u0 < ue; u0 += 32 * UJ) {
                     int bl[UJ];
@@ -427,7 +429,7 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                     }
     #pragma unroll
                     for (int q = 0; q < UJ; q++)
-                        if (bl[q] >= 0) w[bl[q]] -= l * bv[q];
+                        if (u0 + 32 * q < ue && bl[q] >= 0) w[bl[q]] -= l * bv[q];
                 }
                 __syncwarp();
                 if (lane == 0) w[t] = l;
@@ -685,21 +687,31 @@ __device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg 
 // Warp 0 (the walker) solves block b row after row: lane j owns row j of the
 // block, the result of lane s is broadcast and every lane applies the diag
 // entry of its row to it (and the late entry of its row in block b + 1, so the
-// late part of the next block is complete when this block is).  Warps 1..
-// (the helpers) meanwhile gather block b + 1: the right-hand side minus the
-// early part (a warp per row, external sources polled in global memory) and
-// the two 32 x 32 tiles of diag / late entries the walker reads next.  One
-// CTA barrier per block; the per-row hand-off is a shuffle instead of a
-// global-memory round trip, and the bulk of the dot products runs on the
-// helpers, off the chain of dependent steps.
+// late part of the next block is complete when this block is).  The other
+// warps (the helpers) meanwhile gather block b + 1: the right-hand side minus
+// the early part (a warp per row, external sources polled in global memory)
+// and the two 32 x 32 tiles of diag / late entries the walker reads next.
+// Where the phase divides by the pivot, the helpers fold the reciprocal pivot
+// of each row into its tile rows and right-hand side, so a walker step is one
+// shuffle and one multiply-add.  One CTA barrier per block; the per-row
+// hand-off is a shuffle instead of a global-memory round trip, and the bulk of
+// the dot products runs on the helpers, off the chain of dependent steps.
 constexpr int CB = 32;
 constexpr int TS = CB + 1;
+constexpr int CHAIN_MIN = 24;     // shortest task given a CTA
+constexpr int ZCAP_MAX = 8192;    // rows of a CTA task cached in shared memory
+constexpr size_t CHAIN_SMEM = 200 * 1024;   // shared-memory budget of a CTA task
+constexpr int SWARPS = 16;        // warps per CTA of the single-system solves
+constexpr int TJ = 5;             // tile rows a helper loads at once
+constexpr int EJ = 4;             // slots per lane of one early-part chunk
+constexpr int ER = 3;             // early-part rows a helper works on at once
+constexpr int EJ2 = 8;            // slots per lane of the further chunks of a long row
 
-constexpr int CHAIN_MIN = 64;     // shortest task given a CTA
-constexpr int ZCAP_MAX = 8192;    // results of a CTA task kept in shared memory
-
-__host__ __device__ constexpr size_t chain_smem_words(int zcap) {
-    return (size_t)4 * CB * TS + 2 * CB + (size_t)zcap;
+// shared memory of a CTA task, in bytes: tiles, right-hand sides and results
+// (T), and per row up to zcap: the right-hand side term, the pivot scale (T)
+// and four slot bounds (int)
+__host__ __device__ constexpr size_t chain_smem_bytes(int zcap, size_t tsz) {
+    return ((size_t)4 * CB * TS + 2 * CB + 3 * (size_t)zcap) * tsz + 4 * sizeof(int) * (size_t)zcap;
 }
 
 template <typename T, bool BACKWARD, bool TRANS>
@@ -717,29 +729,59 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
     T *xb = tl + 2 * CB * TS;                  // [2][CB]: right-hand side minus the early part
     T *zs = xb + 2 * CB;                       // [zcap]: results of this task by step
     const int zcap = tk.zcap;
+    T *mb = zs + zcap;                          // [zcap]: right-hand side term by step
+    T *ms = mb + zcap;                          // [zcap]: pivot scale (1 without division)
+    int4 *mi = reinterpret_cast<int4 *>(ms + zcap);   // [zcap]: slot bounds (see meta)
     auto row_of = [&](int k) { return BACKWARD ? hi - k : lo + k; };
     auto step_of = [&](int c) { return BACKWARD ? hi - c : c - lo; };
-    // value of source column c (a step of this task before the current block,
-    // or another task's published result)
-    auto source = [&](int c, bool &pending) -> T {
-        pending = false;
-        if (c >= lo && c <= hi) {
-            const int st = step_of(c);
-            return st < zcap ? zs[st] : yout[c];
-        }
-        const T v = ld_relaxed_v(yout + c);
-        pending = is_marker(v);
-        return v;
-    };
-    // the three slot ranges of row i (forward: [tb, e) early, [e, d) late,
-    // [d, te) diag; backward: [tb, d) diag, [d, e) late, [e, te) early)
-    auto ranges = [&](int i, int &tb, int &e, int &d, int &te) {
+    // Slot bounds of the row at step k: x = first slot of the dependency
+    // range, y = cs_late, z = cs_diag, w = end of the range (forward: early
+    // [x, y), late [y, z), diag [z, w); backward: diag [x, z), late [z, y),
+    // early [y, w)), its right-hand side term and pivot scale; cached in
+    // shared memory by the prologue below for steps < zcap.
+    auto meta_g = [&](int k, int4 &q, T &base, T &scl) {
+        const int i = row_of(k);
         const int dg = P.diag[i];
-        tb = BACKWARD ? dg + 1 : P.lu_rp[i];
-        te = BACKWARD ? P.lu_rp[i + 1] : dg;
-        e = tk.cs_late[i];
-        d = tk.cs_diag[i];
+        q.x = BACKWARD ? dg + 1 : P.lu_rp[i];
+        q.w = BACKWARD ? P.lu_rp[i + 1] : dg;
+        q.y = tk.cs_late[i];
+        q.z = tk.cs_diag[i];
+        if (BACKWARD) base = yin[i];
+        else base = (T)(sp[i] * rhs[P.perm[i]]);
+        scl = DIV ? rcp[i] : T(1);
     };
+    auto meta = [&](int k, int4 &q, T &base, T &scl) {
+        if (k < zcap) {
+            q = mi[k];
+            base = mb[k];
+            scl = ms[k];
+        } else {
+            meta_g(k, q, base, scl);
+        }
+    };
+    {
+        const int mm = min(m, zcap);
+        constexpr int U = 4;
+        for (int k0 = threadIdx.x; k0 < mm; k0 += U * blockDim.x) {
+            int4 q[U];
+            T bs[U], sc[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int k = k0 + u * blockDim.x;
+                if (k < mm) meta_g(k, q[u], bs[u], sc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int k = k0 + u * blockDim.x;
+                if (k < mm) {
+                    mi[k] = q[u];
+                    mb[k] = bs[u];
+                    ms[k] = sc[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
 
     // helpers: prepare block B (x - early, diag tile) and the late tile of block B + 1
     auto prepare = [&](int B) {
@@ -747,69 +789,207 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
         const int nh = nw - 1, h = wid - 1;
         T *tdb = td + (B & 1) * CB * TS, *tlb = tl + (B & 1) * CB * TS, *xbb = xb + (B & 1) * CB;
         const int k0 = B * CB, cnt = min(CB, m - k0);
-        for (int j = h; j < cnt; j += nh) {
-            const int i = row_of(k0 + j);
-            int tb, e, d, te;
-            ranges(i, tb, e, d, te);
-            // diag tile row j
-            for (int s = lane; s < TS; s += 32) tdb[j * TS + s] = T(0);
-            __syncwarp();
-            const int db = BACKWARD ? tb : d, de = BACKWARD ? d : te;
-            for (int t = db + lane; t < de; t += 32) tdb[j * TS + step_of(P.lu_ci[t]) - k0] = F[t];
-            // early part: a dot product over [eb, ee)
-            const int eb = BACKWARD ? e : tb, ee = BACKWARD ? te : e;
-            T acc = T(0);
-            for (int t0 = eb; t0 < ee; t0 += 32 * 4) {
-                int cc[4];
-                T fv[4], v[4];
-                unsigned need = 0;
+        const int cnt1 = (B + 1 < nb) ? min(CB, m - k0 - CB) : 0;
+        // tile rows: jobs [0, cnt) diag rows of block B, [CB, CB + cnt1) late rows of block B + 1
+        for (int j0 = h; j0 < 2 * CB; j0 += nh * TJ) {
+            int sb[TJ], se[TJ], jr[TJ];
+            T sc[TJ];
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const int t = t0 + 32 * q + lane;
-                    cc[q] = -1;
-                    fv[q] = T(0);
-                    v[q] = T(0);
-                    if (t < ee) {
-                        cc[q] = P.lu_ci[t];
-                        fv[q] = F[t];
+            for (int q = 0; q < TJ; q++) {     // row metadata of every job first
+                const int job = j0 + q * nh;
+                jr[q] = -1;
+                sb[q] = se[q] = 0;
+                sc[q] = T(1);
+                const bool dg = job < CB;
+                const int j = dg ? job : job - CB;
+                if (job < 2 * CB && j < (dg ? cnt : cnt1)) {
+                    int4 mt;
+                    T bs_;
+                    meta(dg ? k0 + j : k0 + CB + j, mt, bs_, sc[q]);
+                    jr[q] = job;
+                    if (dg) {
+                        sb[q] = BACKWARD ? mt.x : mt.z;
+                        se[q] = BACKWARD ? mt.z : mt.w;
+                    } else {
+                        sb[q] = BACKWARD ? mt.z : mt.y;
+                        se[q] = BACKWARD ? mt.y : mt.z;
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    if (cc[q] >= 0) {
-                        bool pend;
-                        v[q] = source(cc[q], pend);
-                        if (pend) need |= 1u << q;
-                    }
-                }
-                if (__any_sync(FULL, need != 0)) {
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const bool nq = (need >> q) & 1u;
-                        const T w = warp_wait_load(rc, yout + (nq ? cc[q] : 0), nq, lane);
-                        if (nq) v[q] = w;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; q++) acc += fv[q] * v[q];
             }
-            acc = warp_sum(acc);
-            if (lane == 0) {
-                const T base = BACKWARD ? yin[i] : (T)(sp[i] * rhs[P.perm[i]]);
-                xbb[j] = base - acc;
+            int cc[TJ];
+            T fv[TJ];
+#pragma unroll
+            for (int q = 0; q < TJ; q++) {     // then every slot (at most 31 per row)
+                cc[q] = -1;
+                fv[q] = T(0);
+                if (jr[q] >= 0 && sb[q] + lane < se[q]) {
+                    cc[q] = P.lu_ci[sb[q] + lane];
+                    fv[q] = F[sb[q] + lane];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < TJ; q++) {
+                if (jr[q] < 0) continue;
+                const bool dg = jr[q] < CB;
+                T *row = dg ? tdb + jr[q] * TS : tlb + (jr[q] - CB) * TS;
+                row[lane] = T(0);
+                if (lane == 0) row[CB] = T(0);
+                __syncwarp();
+                if (cc[q] >= 0) row[step_of(cc[q]) - k0] = fv[q] * sc[q];
             }
         }
-        // late tile of block B + 1 (sources in block B)
-        if (B + 1 < nb) {
-            const int k1 = k0 + CB, cnt1 = min(CB, m - k1);
-            for (int j = h; j < cnt1; j += nh) {
-                const int i = row_of(k1 + j);
-                int tb, e, d, te;
-                ranges(i, tb, e, d, te);
-                for (int s = lane; s < TS; s += 32) tlb[j * TS + s] = T(0);
-                __syncwarp();
-                const int lb = BACKWARD ? d : e, le = BACKWARD ? e : d;
-                for (int t = lb + lane; t < le; t += 32) tlb[j * TS + step_of(P.lu_ci[t]) - k0] = F[t];
+        // early parts: a warp per row, ER rows of a helper at once (their first
+        // 32 x EJ slots loaded together, then their sources, then one
+        // interleaved reduction); rows with more early slots finish chunk by
+        // chunk.
+        for (int j0 = h; j0 < cnt; j0 += ER * nh) {
+            int eb[ER], ee[ER];
+            T base[ER], scl[ER], acc[ER];
+            int cc[ER][EJ];
+            T fv[ER][EJ];
+#pragma unroll
+            for (int r = 0; r < ER; r++) {
+                const int j = j0 + r * nh;
+                eb[r] = ee[r] = 0;
+                base[r] = T(0);
+                scl[r] = T(1);
+                acc[r] = T(0);
+                if (j < cnt) {
+                    int4 mt;
+                    meta(k0 + j, mt, base[r], scl[r]);
+                    eb[r] = BACKWARD ? mt.y : mt.x;
+                    ee[r] = BACKWARD ? mt.w : mt.y;
+                }
+            }
+            int t0r[ER];
+            auto load_chunk = [&](int r, int t0) {
+                t0r[r] = t0;
+#pragma unroll
+                for (int q = 0; q < EJ; q++) {
+                    const int t = t0 + 32 * q + lane;
+                    cc[r][q] = -1;
+                    fv[r][q] = T(0);
+                    if (t < ee[r]) {
+                        cc[r][q] = P.lu_ci[t];
+                        fv[r][q] = F[t];
+                    }
+                }
+            };
+            // value of every loaded slot (inside the task from shared memory),
+            // then the polls of sources not yet published, then the products
+            T v[ER][EJ];
+            unsigned need[ER];
+            auto gather = [&](int r) {
+                need[r] = 0;
+#pragma unroll
+                for (int q = 0; q < EJ; q++) {
+                    const int c = cc[r][q];
+                    v[r][q] = T(0);
+                    if (c >= 0) {
+                        if (c >= lo && c <= hi) {
+                            const int st = step_of(c);
+                            v[r][q] = st < zcap ? zs[st] : yout[c];
+                        } else {
+                            v[r][q] = ld_relaxed_v(yout + c);
+                        }
+                    }
+                }
+            };
+            auto finish = [&](int r) {
+#pragma unroll
+                for (int q = 0; q < EJ; q++)
+                    if (cc[r][q] >= 0 && is_marker(v[r][q])) need[r] |= 1u << q;
+                if (__any_sync(FULL, need[r] != 0)) {
+#pragma unroll
+                    for (int q = 0; q < EJ; q++) {
+                        const bool nq = (need[r] >> q) & 1u;
+                        const T w = warp_wait_load(rc, yout + (nq ? cc[r][q] : 0), nq, lane);
+                        if (nq) v[r][q] = w;
+                    }
+                }
+                // FP64 instructions cost the same with idle lanes: skip the
+                // rounds past the end of the row
+                const int tq = ee[r] - t0r[r];
+#pragma unroll
+                for (int q = 0; q < EJ; q++)
+                    if (32 * q < tq) acc[r] = fma(fv[r][q], v[r][q], acc[r]);
+            };
+#pragma unroll
+            for (int r = 0; r < ER; r++) load_chunk(r, eb[r]);
+#pragma unroll
+            for (int r = 0; r < ER; r++) gather(r);
+#pragma unroll
+            for (int r = 0; r < ER; r++) finish(r);
+            // longer rows: the rest in chunks of 32 x EJ2, the next chunk's
+            // slots in flight while this one's sources are read
+#pragma unroll
+            for (int r = 0; r < ER; r++) {
+                int t0 = eb[r] + 32 * EJ;
+                if (t0 >= ee[r]) continue;
+                int c1[EJ2];
+                T f1[EJ2];
+                auto load2 = [&](int tb, int (&c)[EJ2], T (&f)[EJ2]) {
+#pragma unroll
+                    for (int q = 0; q < EJ2; q++) {
+                        const int t = tb + 32 * q + lane;
+                        c[q] = -1;
+                        f[q] = T(0);
+                        if (t < ee[r]) {
+                            c[q] = P.lu_ci[t];
+                            f[q] = F[t];
+                        }
+                    }
+                };
+                load2(t0, c1, f1);
+                for (; t0 < ee[r]; t0 += 32 * EJ2) {
+                    int c2[EJ2];
+                    T f2[EJ2], w2[EJ2];
+                    if (t0 + 32 * EJ2 < ee[r]) load2(t0 + 32 * EJ2, c2, f2);
+                    unsigned nd = 0;
+#pragma unroll
+                    for (int q = 0; q < EJ2; q++) {
+                        const int c = c1[q];
+                        w2[q] = T(0);
+                        if (c >= 0) {
+                            if (c >= lo && c <= hi) {
+                                const int st = step_of(c);
+                                w2[q] = st < zcap ? zs[st] : yout[c];
+                            } else {
+                                w2[q] = ld_relaxed_v(yout + c);
+                                if (is_marker(w2[q])) nd |= 1u << q;
+                            }
+                        }
+                    }
+                    if (__any_sync(FULL, nd != 0)) {
+#pragma unroll
+                        for (int q = 0; q < EJ2; q++) {
+                            const bool nq = (nd >> q) & 1u;
+                            const T w = warp_wait_load(rc, yout + (nq ? c1[q] : 0), nq, lane);
+                            if (nq) w2[q] = w;
+                        }
+                    }
+                    const int tq = ee[r] - t0;
+#pragma unroll
+                    for (int q = 0; q < EJ2; q++)
+                        if (32 * q < tq) acc[r] = fma(f1[q], w2[q], acc[r]);
+#pragma unroll
+                    for (int q = 0; q < EJ2; q++) {
+                        c1[q] = c2[q];
+                        f1[q] = f2[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int r = 0; r < ER; r++) acc[r] += __shfl_xor_sync(FULL, acc[r], o);
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int r = 0; r < ER; r++) {
+                    const int j = j0 + r * nh;
+                    if (j < cnt) xbb[j] = (base[r] - acc[r]) * scl[r];
+                }
             }
         }
     };
@@ -823,23 +1003,20 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
             const T *tlb = tl + (b & 1) * CB * TS + lane * TS;
             const int k0 = b * CB, cnt = min(CB, m - k0);
             const bool own = lane < cnt;
-            const int i = own ? row_of(k0 + lane) : row_of(k0);
-            T orc = T(1);
-            if (DIV && own) orc = rcp[i];
             T acc = own ? xb[(b & 1) * CB + lane] + late : T(0);
             late = T(0);
             T z = T(0);
 #pragma unroll
             for (int s = 0; s < CB; s++) {
                 if (s < cnt) {
-                    T zl = DIV ? acc * orc : acc;
-                    const T zb = __shfl_sync(FULL, zl, s);
-                    if (lane == s) z = zl;
+                    const T zb = __shfl_sync(FULL, acc, s);
+                    if (lane == s) z = acc;
                     acc = fma(-tdb[s], zb, acc);
                     late = fma(-tlb[s], zb, late);
                 }
             }
             if (own) {
+                const int i = row_of(k0 + lane);
                 if (is_marker(z)) {
                     z = T(NAN);
                     atomicExch(rc.status + ST_NONFINITE, 1);
@@ -861,7 +1038,7 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
 }
 
 template <typename T, bool BACKWARD, bool TRANS>
-__global__ void __launch_bounds__(WARPS * 32, 2)
+__global__ void __launch_bounds__(SWARPS * 32, 1)
 k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T *__restrict__ rcp,
            const double *__restrict__ rhs, const double *__restrict__ sp, const T *__restrict__ yin,
            T *yout, double *__restrict__ out, int accumulate) {
@@ -1446,7 +1623,7 @@ struct kkt_ctx {
     const int *cs_fwd = nullptr, *csd_fwd = nullptr, *cs_bwd = nullptr, *csd_bwd = nullptr;
     size_t solve_smem = 0;
     unsigned long long *h_norms = nullptr;  // pinned
-    int grid = 0, solve_grid = 0, cta_warps = WARPS, cap = 0;
+    int grid = 0, solve_grid = 0, bsolve_grid = 0, cta_warps = WARPS, solve_warps = SWARPS, cap = 0;
     size_t smem = 0, device_bytes = 0;
     long long nnz_lu = 0;
     std::vector<int> at_rp, at_src;
@@ -1613,8 +1790,13 @@ static kkt_status upload(kkt_ctx *c) {
     const int rows_cap = (n + nw - 1) / nw;
     int grid = c->opt.refactor_ctas > 0 ? std::min(c->opt.refactor_ctas, sms * per_sm) : sms * per_sm;
     c->grid = std::max(1, std::min(grid, rows_cap));
-    int sgrid = c->opt.solve_ctas > 0 ? c->opt.solve_ctas : sms * 2;
-    c->solve_grid = std::max(1, std::min(sgrid, rows_cap));
+    // batched solves: 2 CTAs of cta_warps per SM; single-system solves: CTAs of
+    // twice as many warps, one per SM (a CTA task gets the whole SM)
+    c->bsolve_grid = std::max(1, std::min(sms * 2, rows_cap));
+    c->solve_warps = 2 * nw;
+    const int snw = c->solve_warps;
+    int sgrid = c->opt.solve_ctas > 0 ? c->opt.solve_ctas : sms;
+    c->solve_grid = std::max(1, std::min(sgrid, (n + snw - 1) / snw));
     // rows longer than the shared-memory capacity work in global scratch
     if (a.max_row > cap) {
         size_t per = (size_t)a.max_row;
@@ -1637,14 +1819,17 @@ static kkt_status upload(kkt_ctx *c) {
     // solve tasks: claim orders and shared-memory capacity
     {
         const int nt = (int)a.task_lo.size();
-        std::vector<int> len(nt), top(nt);
+        std::vector<int> len(nt), top(nt), depth(nt);
         for (int T = 0; T < nt; T++) {
             len[T] = a.task_hi[T] - a.task_lo[T] + 1;
             top[T] = a.level[a.task_hi[T]];
+            depth[T] = a.level_u[a.task_hi[T]];
         }
         // Claim orders over a set of tasks: forward = the longest tasks (fewer
-        // than a quarter of the resident warps) first, then by level of the top
-        // row; backward = from the root; topological = by level only.
+        // than a quarter of the resident warps) first, then the deepest top
+        // rows first (critical path first; a task depends only on deeper
+        // tasks); backward = by height of the top row, from the root;
+        // topological = deepest top rows first.
         auto orders = [&](const std::vector<int> &set, long long warps, std::vector<int> &of,
                           std::vector<int> &ob, std::vector<int> &ot) {
             std::vector<int> bylen(set);
@@ -1667,23 +1852,23 @@ static kkt_status upload(kkt_ctx *c) {
             std::stable_sort(of.begin(), of.end(), [&](int x, int y) {
                 const bool lx = len[x] >= lmin, ly = len[y] >= lmin;
                 if (lx != ly) return lx;
-                return top[x] < top[y];
+                return depth[x] > depth[y];
             });
             std::stable_sort(ob.begin(), ob.end(), [&](int x, int y) { return top[x] > top[y]; });
-            std::stable_sort(ot.begin(), ot.end(), [&](int x, int y) { return top[x] < top[y]; });
+            std::stable_sort(ot.begin(), ot.end(), [&](int x, int y) { return depth[x] > depth[y]; });
         };
         std::vector<int> all(nt);
         std::iota(all.begin(), all.end(), 0);
         std::vector<int> of, ob, ot;
-        orders(all, (long long)c->solve_grid * nw, of, ob, ot);
+        orders(all, (long long)c->bsolve_grid * nw, of, ob, ot);
         // Single-system solves: the longest tasks (at least CHAIN_MIN rows, at
         // most a quarter of the CTAs) run on a CTA each; the rest are claimed
         // by warps.
         std::vector<int> chain, reg;
-        if (nw >= 4 && c->solve_grid >= 8) {
+        if (snw >= 8 && c->solve_grid >= 6) {
             std::vector<int> bylen(all);
             std::stable_sort(bylen.begin(), bylen.end(), [&](int x, int y) { return len[x] > len[y]; });
-            const int max_chain = c->solve_grid / 4;
+            const int max_chain = c->solve_grid / 3;
             for (int T : bylen) {
                 if ((int)chain.size() >= max_chain || len[T] < CHAIN_MIN) break;
                 chain.push_back(T);
@@ -1696,7 +1881,7 @@ static kkt_status upload(kkt_ctx *c) {
                 if (!is_chain[T]) reg.push_back(T);
         }
         std::vector<int> of1, ob1, ot1;
-        orders(reg, (long long)(c->solve_grid - (int)chain.size()) * nw, of1, ob1, ot1);
+        orders(reg, (long long)(c->solve_grid - (int)chain.size()) * snw, of1, ob1, ot1);
         // slot splits of the rows of CTA tasks (forward / backward phases share
         // them: cs_late and cs_diag are column bounds turned into slots)
         int zmax = 0;
@@ -1765,10 +1950,15 @@ static kkt_status upload(kkt_ctx *c) {
         int max_reg = 1;
         for (int T : reg) max_reg = std::max(max_reg, len[T]);
         c->tk1.cap = std::min(max_reg, 1024);
-        c->tk1.zcap = std::min(zmax, ZCAP_MAX);
+        {   // rows of a CTA task cached in shared memory: all of the longest
+            // task if the CTA's shared memory allows, a multiple of 4 (alignment)
+            const size_t fixed = chain_smem_bytes(0, tsz), per = chain_smem_bytes(1, tsz) - fixed;
+            const int zfit = (int)((CHAIN_SMEM - fixed) / per) & ~3;
+            c->tk1.zcap = std::min((zmax + 3) & ~3, std::min(zfit, ZCAP_MAX));
+        }
         c->device_bytes += words * sizeof(int);
-        c->solve_smem = std::max((size_t)nw * c->tk1.cap * tsz,
-                                 c->tk1.nchain ? chain_smem_words(c->tk1.zcap) * tsz : 0);
+        c->solve_smem = std::max((size_t)snw * c->tk1.cap * tsz,
+                                 c->tk1.nchain ? chain_smem_bytes(c->tk1.zcap, tsz) : 0);
         auto setsm = [&](const void *f) {
             return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->solve_smem);
         };
@@ -1779,14 +1969,14 @@ static kkt_status upload(kkt_ctx *c) {
             CK(setsm((const void *)k_trisolve<float, false, true>));
             CK(setsm((const void *)k_trisolve<float, true, true>));
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_trisolve<float, false, false>,
-                                                             nw * 32, c->solve_smem));
+                                                             snw * 32, c->solve_smem));
         } else {
             CK(setsm((const void *)k_trisolve<double, false, false>));
             CK(setsm((const void *)k_trisolve<double, true, false>));
             CK(setsm((const void *)k_trisolve<double, false, true>));
             CK(setsm((const void *)k_trisolve<double, true, true>));
             CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, k_trisolve<double, false, false>,
-                                                             nw * 32, c->solve_smem));
+                                                             snw * 32, c->solve_smem));
         }
         // every CTA of a solve must be resident at once (CTA tasks and waiting warps)
         if ((long long)per_sm_s * sms < c->solve_grid) {
@@ -1965,11 +2155,11 @@ static kkt_status launch_solve(kkt_ctx *c, const double *b, double *x, int accum
     T *y = (T *)c->d_y, *z = y + n;
     const T *L = (const T *)c->d_lu, *R = (const T *)c->d_rcp;
     CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
-    k_trisolve<T, false, false><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
+    k_trisolve<T, false, false><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
         c->P, c->rc, tasks_of(c, false), L, R, b, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
     c->launches++;
-    k_trisolve<T, true, false><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
+    k_trisolve<T, true, false><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
         c->P, c->rc, tasks_of(c, true), L, R, nullptr, c->d_sp, y, z, x, accumulate);
     CK(cudaGetLastError());
     c->launches++;
@@ -1983,11 +2173,11 @@ static kkt_status launch_solve_t(kkt_ctx *c, const double *g, double *lam, int a
     T *y = (T *)c->d_y, *z = y + n;
     const T *L = (const T *)c->d_lut, *R = (const T *)c->d_rcp;
     CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
-    k_trisolve<T, false, true><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
+    k_trisolve<T, false, true><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
         c->P, c->rc, tasks_of(c, false), L, R, g, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
     c->launches++;
-    k_trisolve<T, true, true><<<c->solve_grid, c->cta_warps * 32, c->solve_smem, s>>>(
+    k_trisolve<T, true, true><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
         c->P, c->rc, tasks_of(c, true), L, R, nullptr, c->d_sp, y, z, lam, accumulate);
     CK(cudaGetLastError());
     c->launches++;
@@ -2298,18 +2488,18 @@ static kkt_status launch_bsolve(kkt_ctx *c, int B, const double *b, double *x, i
     const T *F = (const T *)(transpose ? c->b_lut : c->b_lu), *R = (const T *)c->b_rcp;
     CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * B * sizeof(T), s));
     if (transpose) {
-        k_btrisolve<T, false, true><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(
+        k_btrisolve<T, false, true><<<c->bsolve_grid, c->cta_warps * 32, 0, s>>>(
             c->P, c->rc, c->tk, B, F, R, b, c->b_sp, nullptr, y, nullptr, 0);
         CK(cudaGetLastError());
         c->launches++;
-        k_btrisolve<T, true, true><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(
+        k_btrisolve<T, true, true><<<c->bsolve_grid, c->cta_warps * 32, 0, s>>>(
             c->P, c->rc, c->tk, B, F, R, nullptr, c->b_sp, y, z, x, accumulate);
     } else {
-        k_btrisolve<T, false, false><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(
+        k_btrisolve<T, false, false><<<c->bsolve_grid, c->cta_warps * 32, 0, s>>>(
             c->P, c->rc, c->tk, B, F, R, b, c->b_sp, nullptr, y, nullptr, 0);
         CK(cudaGetLastError());
         c->launches++;
-        k_btrisolve<T, true, false><<<c->solve_grid, c->cta_warps * 32, 0, s>>>(
+        k_btrisolve<T, true, false><<<c->bsolve_grid, c->cta_warps * 32, 0, s>>>(
             c->P, c->rc, c->tk, B, F, R, nullptr, c->b_sp, y, z, x, accumulate);
     }
     CK(cudaGetLastError());
