@@ -60,6 +60,11 @@ struct TaskCfg {
     int zcap;                            // results of a CTA task kept in shared memory
     const int *chain_task;
     const int *cs_late, *cs_diag;
+    // Per refactorization, the 32 x 32 tiles of every block of every CTA task
+    // are packed for each solve phase (see k_pack_tiles): block b of CTA task
+    // c is block chain_blk0[c] + b of this phase's tile array.
+    const int *chain_blk0;
+    const void *tiles;
 };
 
 struct RunCfg {

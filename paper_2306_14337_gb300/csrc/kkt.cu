@@ -251,6 +251,12 @@ template <typename T> __device__ __forceinline__ void publish(const RunCfg &rc, 
     st_relaxed_v(p, v);
 }
 
+// Barrier over the first `threads` threads... of the warps that reach it: a
+// named barrier (id 1..15) shared by a subset of the CTA's warps.
+__device__ __forceinline__ void named_barrier(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
@@ -403,11 +409,9 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
     #pragma unroll
                 for (int q = 0; q < UJ; q++)
                     if (32 * q < ue - ub - 1 && lo[q] >= 0) w[lo[q]] -= l * uv[q];
-                // remaining blocks of long pivot rows
-                for (int u0 = ub + 1 + 32 * UJ; u0 < ue; u0 += 32 * UJ) {
-                    int bl[UJ];
-                    T bv[UJ];
-                    unsigned bneed = 0;
+                // remaining blocks of long pivot rows, double-buffered: the next
+                // block's targets and values are in flight while this one updates
+                auto load_blk = [&](int u0, int (&bl)[UJ], T (&bv)[UJ]) {
     #pragma unroll
                     for (int q = 0; q < UJ; q++) {
                         const int u = u0 + 32 * q + lane;
@@ -416,20 +420,38 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                         if (u < ue) {
                             bl[q] = target(t, ub, mo, u);
                             bv[q] = ld_relaxed_v(LU + u);
-                            if (is_marker(bv[q])) bneed |= 1u << q;
                         }
                     }
-                    if (__any_sync(FULL, bneed != 0)) {
+                };
+                if (ub + 1 + 32 * UJ < ue) {
+                    int cl[UJ];
+                    T cv[UJ];
+                    load_blk(ub + 1 + 32 * UJ, cl, cv);
+                    for (int u0 = ub + 1 + 32 * UJ; u0 < ue; u0 += 32 * UJ) {
+                        int nl[UJ];
+                        T nv[UJ];
+                        if (u0 + 32 * UJ < ue) load_blk(u0 + 32 * UJ, nl, nv);
+                        unsigned bneed = 0;
+    #pragma unroll
+                        for (int q = 0; q < UJ; q++)
+                            if (cl[q] >= 0 && is_marker(cv[q])) bneed |= 1u << q;
+                        if (__any_sync(FULL, bneed != 0)) {
+    #pragma unroll
+                            for (int q = 0; q < UJ; q++) {
+                                const bool nq = (bneed >> q) & 1u;
+                                const T v = warp_wait_load(rc, LU + (nq ? u0 + 32 * q + lane : ub), nq, lane);
+                                if (nq) cv[q] = v;
+                            }
+                        }
+    #pragma unroll
+                        for (int q = 0; q < UJ; q++)
+                            if (u0 + 32 * q < ue && cl[q] >= 0) w[cl[q]] -= l * cv[q];
     #pragma unroll
                         for (int q = 0; q < UJ; q++) {
-                            const bool nq = (bneed >> q) & 1u;
-                            const T v = warp_wait_load(rc, LU + (nq ? u0 + 32 * q + lane : ub), nq, lane);
-                            if (nq) bv[q] = v;
+                            cl[q] = nl[q];
+                            cv[q] = nv[q];
                         }
                     }
-    #pragma unroll
-                    for (int q = 0; q < UJ; q++)
-                        if (u0 + 32 * q < ue && bl[q] >= 0) w[bl[q]] -= l * bv[q];
                 }
                 __syncwarp();
                 if (lane == 0) w[t] = l;
@@ -702,7 +724,6 @@ constexpr int CHAIN_MIN = 24;     // shortest task given a CTA
 constexpr int ZCAP_MAX = 8192;    // rows of a CTA task cached in shared memory
 constexpr size_t CHAIN_SMEM = 200 * 1024;   // shared-memory budget of a CTA task
 constexpr int SWARPS = 16;        // warps per CTA of the single-system solves
-constexpr int TJ = 5;             // tile rows a helper loads at once
 constexpr int EJ = 4;             // slots per lane of one early-part chunk
 constexpr int ER = 3;             // early-part rows a helper works on at once
 constexpr int EJ2 = 8;            // slots per lane of the further chunks of a long row
@@ -711,7 +732,7 @@ constexpr int EJ2 = 8;            // slots per lane of the further chunks of a l
 // (T), and per row up to zcap: the right-hand side term, the pivot scale (T)
 // and four slot bounds (int)
 __host__ __device__ constexpr size_t chain_smem_bytes(int zcap, size_t tsz) {
-    return ((size_t)4 * CB * TS + 2 * CB + 3 * (size_t)zcap) * tsz + 4 * sizeof(int) * (size_t)zcap;
+    return ((size_t)5 * CB * TS + 6 * CB + 3 * (size_t)zcap) * tsz + 4 * sizeof(int) * (size_t)zcap;
 }
 
 template <typename T, bool BACKWARD, bool TRANS>
@@ -722,13 +743,17 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
                                                T *yout, double *__restrict__ out, int accumulate,
                                                unsigned char *smem) {
     constexpr bool DIV = (TRANS != BACKWARD);
+    constexpr bool FOLD = DIV && sizeof(T) == 8;   // pivots folded into the tiles (FP64)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int m = hi - lo + 1, nb = (m + CB - 1) / CB;
     T *td = reinterpret_cast<T *>(smem);       // [2][CB][TS]: diag entries of a block's rows
     T *tl = td + 2 * CB * TS;                  // [2][CB][TS]: late entries of the next block's rows
     T *xb = tl + 2 * CB * TS;                  // [2][CB]: right-hand side minus the early part
-    T *zs = xb + 2 * CB;                       // [zcap]: results of this task by step
+    T *red = xb + 2 * CB;                      // [CB][TS]: per-lane partial early sums
+    T *sub = red + CB * TS;                    // [4][CB]: partial sums of 8 lanes each
+    T *zs = sub + 4 * CB;                      // [zcap]: results of this task by step
     const int zcap = tk.zcap;
+    const T *tiles = reinterpret_cast<const T *>(tk.tiles) + (size_t)tk.chain_blk0[blockIdx.x] * 2 * CB * CB;
     T *mb = zs + zcap;                          // [zcap]: right-hand side term by step
     T *ms = mb + zcap;                          // [zcap]: pivot scale (1 without division)
     int4 *mi = reinterpret_cast<int4 *>(ms + zcap);   // [zcap]: slot bounds (see meta)
@@ -790,54 +815,32 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
         T *tdb = td + (B & 1) * CB * TS, *tlb = tl + (B & 1) * CB * TS, *xbb = xb + (B & 1) * CB;
         const int k0 = B * CB, cnt = min(CB, m - k0);
         const int cnt1 = (B + 1 < nb) ? min(CB, m - k0 - CB) : 0;
-        // tile rows: jobs [0, cnt) diag rows of block B, [CB, CB + cnt1) late rows of block B + 1
-        for (int j0 = h; j0 < 2 * CB; j0 += nh * TJ) {
-            int sb[TJ], se[TJ], jr[TJ];
-            T sc[TJ];
+        // the two tiles of block B, packed at refactorization: one coalesced
+        // copy (loads first), padded rows in shared memory
+        {
+            const T *src = tiles + (size_t)B * 2 * CB * CB;
+            const int ht = h * 32 + lane, nt = nh * 32;
+            constexpr int TQ = (2 * CB * CB + 32 * 8 - 1) / (32 * 8);   // per thread with >= 8 helpers
+            T tv[TQ];
 #pragma unroll
-            for (int q = 0; q < TJ; q++) {     // row metadata of every job first
-                const int job = j0 + q * nh;
-                jr[q] = -1;
-                sb[q] = se[q] = 0;
-                sc[q] = T(1);
-                const bool dg = job < CB;
-                const int j = dg ? job : job - CB;
-                if (job < 2 * CB && j < (dg ? cnt : cnt1)) {
-                    int4 mt;
-                    T bs_;
-                    meta(dg ? k0 + j : k0 + CB + j, mt, bs_, sc[q]);
-                    jr[q] = job;
-                    if (dg) {
-                        sb[q] = BACKWARD ? mt.x : mt.z;
-                        se[q] = BACKWARD ? mt.z : mt.w;
-                    } else {
-                        sb[q] = BACKWARD ? mt.z : mt.y;
-                        se[q] = BACKWARD ? mt.y : mt.z;
-                    }
-                }
-            }
-            int cc[TJ];
-            T fv[TJ];
-#pragma unroll
-            for (int q = 0; q < TJ; q++) {     // then every slot (at most 31 per row)
-                cc[q] = -1;
-                fv[q] = T(0);
-                if (jr[q] >= 0 && sb[q] + lane < se[q]) {
-                    cc[q] = P.lu_ci[sb[q] + lane];
-                    fv[q] = F[sb[q] + lane];
-                }
+            for (int q = 0; q < TQ; q++) {
+                const int e = ht + q * nt;
+                tv[q] = e < 2 * CB * CB ? src[e] : T(0);
             }
 #pragma unroll
-            for (int q = 0; q < TJ; q++) {
-                if (jr[q] < 0) continue;
-                const bool dg = jr[q] < CB;
-                T *row = dg ? tdb + jr[q] * TS : tlb + (jr[q] - CB) * TS;
-                row[lane] = T(0);
-                if (lane == 0) row[CB] = T(0);
-                __syncwarp();
-                if (cc[q] >= 0) row[step_of(cc[q]) - k0] = fv[q] * sc[q];
+            for (int q = 0; q < TQ; q++) {
+                const int e = ht + q * nt;
+                if (e < 2 * CB * CB) {
+                    const int tile = e >> 10, j = (e >> 5) & 31, sc_ = e & 31;
+                    (tile ? tlb : tdb)[j * TS + sc_] = tv[q];
+                }
+            }
+            for (int e = ht + TQ * nt; e < 2 * CB * CB; e += nt) {      // fewer helpers
+                const int tile = e >> 10, j = (e >> 5) & 31, sc_ = e & 31;
+                (tile ? tlb : tdb)[j * TS + sc_] = src[e];
             }
         }
+        (void)cnt1;
         // early parts: a warp per row, ER rows of a helper at once (their first
         // 32 x EJ slots loaded together, then their sources, then one
         // interleaved reduction); rows with more early slots finish chunk by
@@ -979,18 +982,29 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
                     }
                 }
             }
+            // per-lane partials to shared memory; summed below across lanes
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                for (int r = 0; r < ER; r++) acc[r] += __shfl_xor_sync(FULL, acc[r], o);
+            for (int r = 0; r < ER; r++) {
+                const int j = j0 + r * nh;
+                if (j < cnt) red[j * TS + lane] = acc[r];
             }
-            if (lane == 0) {
+        }
+        // transposed reduction (a lane per row instead of a shuffle tree per
+        // row: 10 FP64 instructions for the block instead of 5 per row)
+        named_barrier(1, nh * 32);
+        if (h < 4) {
+            T s8 = T(0);
 #pragma unroll
-                for (int r = 0; r < ER; r++) {
-                    const int j = j0 + r * nh;
-                    if (j < cnt) xbb[j] = (base[r] - acc[r]) * scl[r];
-                }
-            }
+            for (int q = 0; q < 8; q++) s8 += red[lane * TS + 8 * h + q];
+            sub[h * CB + lane] = s8;
+        }
+        named_barrier(1, nh * 32);
+        if (h == 0 && lane < cnt) {
+            int4 mt;
+            T base, scl;
+            meta(k0 + lane, mt, base, scl);
+            const T e = (sub[lane] + sub[CB + lane]) + (sub[2 * CB + lane] + sub[3 * CB + lane]);
+            xbb[lane] = FOLD ? (base - e) * scl : base - e;
         }
     };
 
@@ -1004,13 +1018,20 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
             const int k0 = b * CB, cnt = min(CB, m - k0);
             const bool own = lane < cnt;
             T acc = own ? xb[(b & 1) * CB + lane] + late : T(0);
+            T orc = T(1);
+            if (DIV && !FOLD && own) {
+                int4 mt;
+                T bs_;
+                meta(k0 + lane, mt, bs_, orc);
+            }
             late = T(0);
             T z = T(0);
 #pragma unroll
             for (int s = 0; s < CB; s++) {
                 if (s < cnt) {
-                    const T zb = __shfl_sync(FULL, acc, s);
-                    if (lane == s) z = acc;
+                    const T zl = (DIV && !FOLD) ? acc * orc : acc;
+                    const T zb = __shfl_sync(FULL, zl, s);
+                    if (lane == s) z = zl;
                     acc = fma(-tdb[s], zb, acc);
                     late = fma(-tlb[s], zb, late);
                 }
@@ -1034,6 +1055,53 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
             prepare(b + 1);
         }
         __syncthreads();
+    }
+}
+
+// Packs, once per refactorization, the tiles the CTA tasks of the four solve
+// phases read: for every block b of every CTA task, the diag tile (rows of
+// block b, sources in block b) and the late tile (rows of block b + 1, sources
+// in block b), 32 x 32 each, reciprocal pivots folded in where the phase
+// divides (FP64 only: in FP32 the walker's multiply is cheap and one rounding
+// fewer helps refinement).  Phases: 0 forward L (LU), 1 backward U (LU, divides), 2 forward
+// U^T (LUT, divides), 3 backward L^T (LUT).  One warp per tile row.
+template <typename T>
+__global__ void k_pack_tiles(DevPattern P, const int *__restrict__ blk_info, int nblk,
+                             const int *__restrict__ cs_fwd, const int *__restrict__ csd_fwd,
+                             const int *__restrict__ cs_bwd, const int *__restrict__ csd_bwd,
+                             const T *__restrict__ LU, const T *__restrict__ LUT, const T *__restrict__ rcp,
+                             T *__restrict__ tiles) {
+    const int lane = threadIdx.x & 31;
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= 4LL * nblk * 2 * CB) return;
+    const int j = (int)(w & (CB - 1)), which = (int)((w >> 5) & 1);
+    const long long pg = w >> 6;                  // phase * nblk + block
+    const int ph = (int)(pg / nblk), gb = (int)(pg % nblk);
+    const int lo = blk_info[3 * gb], hi = blk_info[3 * gb + 1], b = blk_info[3 * gb + 2];
+    const bool bwd = ph & 1, tr = ph >= 2, div = (ph == 1 || ph == 2);
+    const T *F = tr ? LUT : LU;
+    T *row = tiles + w * CB;
+    row[lane] = T(0);
+    __syncwarp();
+    const int k = CB * (b + which) + j;           // step of the tile row
+    if (k >= hi - lo + 1) return;
+    const int i = bwd ? hi - k : lo + k;
+    const int dg = P.diag[i];
+    int sb, se;
+    if (!bwd) {
+        const int e = cs_fwd[i], d = csd_fwd[i];
+        sb = which ? e : d;
+        se = which ? d : dg;
+    } else {
+        const int e = cs_bwd[i], d = csd_bwd[i];
+        sb = which ? d : dg + 1;
+        se = which ? e : d;
+    }
+    const T scl = (div && sizeof(T) == 8) ? rcp[i] : T(1);   // FP32 divides in the walker
+    const int k0 = CB * b;
+    for (int t = sb + lane; t < se; t += 32) {
+        const int c = P.lu_ci[t];
+        row[(bwd ? hi - c : c - lo) - k0] = F[t] * scl;
     }
 }
 
@@ -1621,6 +1689,10 @@ struct kkt_ctx {
     TaskCfg tk{};             // all tasks (batched and queued solves)
     TaskCfg tk1{};            // single-system solves: CTA tasks + warp tasks
     const int *cs_fwd = nullptr, *csd_fwd = nullptr, *cs_bwd = nullptr, *csd_bwd = nullptr;
+    const int *blk_info = nullptr;   // per block of the CTA tasks: lo, hi, block index
+    int nblk = 0;                    // blocks of all CTA tasks
+    void *d_tiles = nullptr;         // packed tiles, 4 phases x nblk x 2 x 32 x 32
+    bool tiles_fresh = false;        // d_tiles match the current factors
     size_t solve_smem = 0;
     unsigned long long *h_norms = nullptr;  // pinned
     int grid = 0, solve_grid = 0, bsolve_grid = 0, cta_warps = WARPS, solve_warps = SWARPS, cap = 0;
@@ -1882,6 +1954,17 @@ static kkt_status upload(kkt_ctx *c) {
         }
         std::vector<int> of1, ob1, ot1;
         orders(reg, (long long)(c->solve_grid - (int)chain.size()) * snw, of1, ob1, ot1);
+        // blocks of the CTA tasks (for the packed tiles)
+        std::vector<int> blk0(chain.size() + 1, 0), binfo;
+        for (size_t q = 0; q < chain.size(); q++) {
+            const int T = chain[q], nbq = (len[T] + CB - 1) / CB;
+            blk0[q + 1] = blk0[q] + nbq;
+            for (int b = 0; b < nbq; b++) {
+                binfo.push_back(a.task_lo[T]);
+                binfo.push_back(a.task_hi[T]);
+                binfo.push_back(b);
+            }
+        }
         // slot splits of the rows of CTA tasks (forward / backward phases share
         // them: cs_late and cs_diag are column bounds turned into slots)
         int zmax = 0;
@@ -1913,7 +1996,8 @@ static kkt_status upload(kkt_ctx *c) {
             }
         }
         int *d = nullptr;
-        const size_t words = 3 * (size_t)nt + 3 * (size_t)nt + chain.size() + 4 * (size_t)n;
+        const size_t words = 3 * (size_t)nt + 3 * (size_t)nt + chain.size() + 4 * (size_t)n + blk0.size() +
+                             binfo.size();
         CK(cudaMalloc(&d, words * sizeof(int)));
         size_t o = 0;
         auto put = [&](const std::vector<int> &v) -> const int * {
@@ -1938,11 +2022,15 @@ static kkt_status upload(kkt_ctx *c) {
         c->tk1.order_topo = put(ot1);
         c->tk1.nchain = (int)chain.size();
         c->tk1.chain_task = put(chain);
+        c->tk1.chain_blk0 = put(blk0);
+        c->blk_info = put(binfo);
+        c->nblk = blk0.back();
         c->cs_fwd = put(std::vector<int>(csl.begin(), csl.begin() + n));
         c->cs_bwd = put(std::vector<int>(csl.begin() + n, csl.end()));
         c->csd_fwd = put(std::vector<int>(csd.begin(), csd.begin() + n));
         c->csd_bwd = put(std::vector<int>(csd.begin() + n, csd.end()));
-        if (!c->tk.order_f || !c->tk1.order_f || !c->tk1.chain_task || !c->cs_fwd || !c->csd_bwd) {
+        if (!c->tk.order_f || !c->tk1.order_f || !c->tk1.chain_task || !c->cs_fwd || !c->csd_bwd ||
+            !c->tk1.chain_blk0 || !c->blk_info) {
             g_last_error = "copy of the task tables failed";
             return KKT_ERR_CUDA;
         }
@@ -1957,6 +2045,11 @@ static kkt_status upload(kkt_ctx *c) {
             c->tk1.zcap = std::min((zmax + 3) & ~3, std::min(zfit, ZCAP_MAX));
         }
         c->device_bytes += words * sizeof(int);
+        if (c->nblk > 0) {
+            const size_t tb = 4 * (size_t)c->nblk * 2 * CB * CB * tsz;
+            CK(cudaMalloc(&c->d_tiles, tb));
+            c->device_bytes += tb;
+        }
         c->solve_smem = std::max((size_t)snw * c->tk1.cap * tsz,
                                  c->tk1.nchain ? chain_smem_bytes(c->tk1.zcap, tsz) : 0);
         auto setsm = [&](const void *f) {
@@ -2048,6 +2141,7 @@ void kkt_destroy(kkt_ctx *c) {
         cudaFree(c->d_sched);
         cudaFree(c->d_maps);
         cudaFree(c->d_task_orders);
+        cudaFree(c->d_tiles);
         cudaFree(c->d_trace);
         cudaFree(c->d_view_slot);
         cudaFree(c->d_krylov);
@@ -2128,6 +2222,20 @@ kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_
         if ((c)->host_only) { g_last_error = "host-only context"; return KKT_ERR_STATE; } \
     } while (0)
 
+// Packs the CTA tasks' tiles from the current factors (see k_pack_tiles).
+template <typename T> static kkt_status pack_tiles(kkt_ctx *c, cudaStream_t s) {
+    if (c->nblk > 0) {
+        const long long threads = 4LL * c->nblk * 2 * CB * 32;
+        k_pack_tiles<T><<<blocks_for(threads, 256), 256, 0, s>>>(
+            c->P, c->blk_info, c->nblk, c->cs_fwd, c->csd_fwd, c->cs_bwd, c->csd_bwd, (const T *)c->d_lu,
+            (const T *)c->d_lut, (const T *)c->d_rcp, (T *)c->d_tiles);
+        CK(cudaGetLastError());
+        c->launches++;
+    }
+    c->tiles_fresh = true;
+    return KKT_OK;
+}
+
 template <typename T> static kkt_status launch_refactor(kkt_ctx *c, cudaStream_t s) {
     // every entry starts as the not-ready marker; published entries overwrite it
     CK(cudaMemsetAsync(c->d_lu, 0xff, (size_t)c->nnz_lu * sizeof(T), s));
@@ -2137,15 +2245,19 @@ template <typename T> static kkt_status launch_refactor(kkt_ctx *c, cudaStream_t
                                                                (T *)c->d_rcp, c->tau_rel);
     CK(cudaGetLastError());
     c->launches++;
-    return KKT_OK;
+    return pack_tiles<T>(c, s);
 }
 
 // task configuration of a single-system solve phase (the slot splits of CTA
 // tasks depend on the direction of the walk)
-static TaskCfg tasks_of(const kkt_ctx *c, bool backward) {
+static TaskCfg tasks_of(const kkt_ctx *c, bool backward, bool trans) {
     TaskCfg t = c->tk1;
     t.cs_late = backward ? c->cs_bwd : c->cs_fwd;
     t.cs_diag = backward ? c->csd_bwd : c->csd_fwd;
+    const int ph = (trans ? 2 : 0) + (backward ? 1 : 0);
+    const size_t tsz = c->opt.factor_fp32 ? sizeof(float) : sizeof(double);
+    t.tiles = c->d_tiles ? (const void *)((const char *)c->d_tiles + (size_t)ph * c->nblk * 2 * CB * CB * tsz)
+                         : nullptr;
     return t;
 }
 
@@ -2156,11 +2268,11 @@ static kkt_status launch_solve(kkt_ctx *c, const double *b, double *x, int accum
     const T *L = (const T *)c->d_lu, *R = (const T *)c->d_rcp;
     CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
     k_trisolve<T, false, false><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
-        c->P, c->rc, tasks_of(c, false), L, R, b, c->d_sp, nullptr, y, nullptr, 0);
+        c->P, c->rc, tasks_of(c, false, false), L, R, b, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
     c->launches++;
     k_trisolve<T, true, false><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
-        c->P, c->rc, tasks_of(c, true), L, R, nullptr, c->d_sp, y, z, x, accumulate);
+        c->P, c->rc, tasks_of(c, true, false), L, R, nullptr, c->d_sp, y, z, x, accumulate);
     CK(cudaGetLastError());
     c->launches++;
     return KKT_OK;
@@ -2174,11 +2286,11 @@ static kkt_status launch_solve_t(kkt_ctx *c, const double *g, double *lam, int a
     const T *L = (const T *)c->d_lut, *R = (const T *)c->d_rcp;
     CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
     k_trisolve<T, false, true><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
-        c->P, c->rc, tasks_of(c, false), L, R, g, c->d_sp, nullptr, y, nullptr, 0);
+        c->P, c->rc, tasks_of(c, false, true), L, R, g, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
     c->launches++;
     k_trisolve<T, true, true><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
-        c->P, c->rc, tasks_of(c, true), L, R, nullptr, c->d_sp, y, z, lam, accumulate);
+        c->P, c->rc, tasks_of(c, true, true), L, R, nullptr, c->d_sp, y, z, lam, accumulate);
     CK(cudaGetLastError());
     c->launches++;
     return KKT_OK;
@@ -2206,6 +2318,10 @@ kkt_status kkt_refactor(kkt_ctx *c, const double *values_dev, kkt_stream stream)
 
 static kkt_status solve_any(kkt_ctx *c, const double *b, double *x, int accumulate, int transpose,
                             cudaStream_t s) {
+    if (!c->tiles_fresh) {                 // factors written by a queue since the last packing
+        kkt_status r = c->opt.factor_fp32 ? pack_tiles<float>(c, s) : pack_tiles<double>(c, s);
+        if (r != KKT_OK) return r;
+    }
     if (transpose)
         return c->opt.factor_fp32 ? launch_solve_t<float>(c, b, x, accumulate, s)
                                   : launch_solve_t<double>(c, b, x, accumulate, s);
@@ -2882,10 +2998,13 @@ kkt_status kkt_queue_run(kkt_queue *q, const double *const *values, const double
         cudaGraphDestroy(gr);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
         q->key = key;
-        for (int k = 0; k < q->m; k++) {
-            q->ctx[k]->values = values[k];
-            q->ctx[k]->factored = true;
-        }
+    }
+    // every run writes new factors: the contexts' packed tiles are stale until
+    // their next single-system solve packs them again
+    for (int k = 0; k < q->m; k++) {
+        q->ctx[k]->values = values[k];
+        q->ctx[k]->factored = true;
+        q->ctx[k]->tiles_fresh = false;
     }
     CK(cudaGraphLaunch(q->graph, s));
     return KKT_OK;
