@@ -65,6 +65,9 @@ struct TaskCfg {
     // c is block chain_blk0[c] + b of this phase's tile array.
     const int *chain_blk0;
     const void *tiles;
+    // Claim-order entries p < 0 are packs of single-row tasks: pack -1 - p
+    // holds the rows pack_rows[32 (-1 - p) + lane] (-1: empty lane).
+    const int *pack_rows;
 };
 
 struct RunCfg {

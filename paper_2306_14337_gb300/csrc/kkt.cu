@@ -29,6 +29,7 @@
 #include <climits>
 #include <string>
 #include <vector>
+#include <set>
 
 #include "kkt.h"
 #include "analysis.h"
@@ -277,6 +278,20 @@ __device__ __forceinline__ void prefetch_l1(const void *p, long long bytes, int 
 }
 
 // ---------------------------------------------------------------------------
+// Batch-innermost arrays: entry k of system s at p[k * B + s].  The row and
+// task bodies below take either plain pointers (one system) or these (one
+// system of a batch), so the batched kernels run the same code per (row or
+// task, system) as the single-system ones.
+// (Offsets must be summed before they are added: `p + (a + b)`; `p + a`
+// already yields a plain pointer into system s's entry a.)
+template <typename T> struct Strided {
+    T *p;
+    int B, s;
+    __device__ __forceinline__ T *operator+(long long k) const { return p + k * B + s; }
+    __device__ __forceinline__ T &operator[](long long k) const { return p[k * B + s]; }
+};
+
+// ---------------------------------------------------------------------------
 // numeric refactorization: one warp per row of L+U (Algorithm 1's row-wise
 // elimination, fixed pivots), rows claimed deepest first (distance to the root).
 //
@@ -293,10 +308,9 @@ __device__ __forceinline__ void prefetch_l1(const void *p, long long bytes, int 
 // the transposed solves.
 // One row of the refactorization (the warp of lane `lane`); sval / scol are
 // the warp's shared-memory row of capacity rc.cap, gw its global warp index.
-template <typename T>
-__device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &rc,
-                                             const double *__restrict__ aval, const double *__restrict__ sp,
-                                             T *LU, T *LUT, T *rcp, double tau, int i, T *sval, int *scol,
+template <typename T, typename AV = const double *, typename TP = T *>
+__device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &rc, AV aval, AV sp, TP LU,
+                                             TP LUT, TP rcp, double tau, int i, T *sval, int *scol,
                                              int gw, int lane) {
     const bool mapped = P.upd_off != nullptr;
             const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
@@ -396,6 +410,15 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
     #pragma unroll
                 for (int q = 0; q < UJ; q++)
                     if (lo[q] >= 0 && is_marker(uv[q])) need |= 1u << q;
+                if (__any_sync(FULL, need != 0)) {           // one reload of everything still missing
+    #pragma unroll
+                    for (int q = 0; q < UJ; q++)
+                        if ((need >> q) & 1u) uv[q] = ld_relaxed_v(LU + (ub + 1 + 32 * q + lane));
+                    need = 0;
+    #pragma unroll
+                    for (int q = 0; q < UJ; q++)
+                        if (lo[q] >= 0 && is_marker(uv[q])) need |= 1u << q;
+                }
                 if (__any_sync(FULL, need != 0)) {
     #pragma unroll
                     for (int q = 0; q < UJ; q++) {
@@ -470,7 +493,7 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
             }
             __syncwarp();
             // U part first (the signals of the rows below), then the reciprocal pivot
-            for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + rb + t, w[t]);
+            for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + (rb + t), w[t]);
             if (lane == 0) {
                 LU[rb + dp] = w[dp];
                 if (i != rc.unpublished_row) publish(rc, rcp + i, T(1) / w[dp]);
@@ -530,8 +553,8 @@ k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const doubl
 constexpr int SJ = 8;
 
 // Load up to 32 x SJ dependency slots of one row (column, factor value).
-template <typename T>
-__device__ __forceinline__ void load_slots(const DevPattern &P, const T *__restrict__ F, int tb, int te,
+template <typename T, typename FP>
+__device__ __forceinline__ void load_slots(const DevPattern &P, FP F, int tb, int te,
                                            int lane, int (&col)[SJ], T (&val)[SJ]) {
 #pragma unroll
     for (int j = 0; j < SJ; j++) {
@@ -547,11 +570,10 @@ __device__ __forceinline__ void load_slots(const DevPattern &P, const T *__restr
 
 // One task of a triangular solve (the warp of lane `lane`); loc is the warp's
 // shared-memory buffer of capacity tk.cap.
-template <typename T, bool BACKWARD, bool TRANS>
-__device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
-                                              const T *__restrict__ F, const T *__restrict__ rcp,
-                                              const double *__restrict__ rhs, const double *__restrict__ sp,
-                                              const T *__restrict__ yin, T *yout, double *__restrict__ out,
+template <typename T, bool BACKWARD, bool TRANS, typename CF = const T *, typename CD = const double *,
+          typename TF = T *, typename DF = double *>
+__device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk, CF F,
+                                              CF rcp, CD rhs, CD sp, CF yin, TF yout, DF out,
                                               int accumulate, int tid, T *loc, int lane) {
     constexpr bool DIV = (TRANS != BACKWARD);
             const int lo = tk.task_lo[tid], hi = tk.task_hi[tid];
@@ -588,7 +610,7 @@ __device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg 
             owner(lane);
             int ncol[SJ];
             T nval[SJ];
-            load_slots(P, F, __shfl_sync(FULL, ctb, 0), __shfl_sync(FULL, cte, 0), lane, ncol, nval);
+            load_slots<T>(P, F, __shfl_sync(FULL, ctb, 0), __shfl_sync(FULL, cte, 0), lane, ncol, nval);
             for (int k = 0; k < m; k++) {
                 const int kl = k & 31;
                 if (kl == 0 && k > 0) {                      // advance to the next chunk
@@ -607,7 +629,7 @@ __device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg 
                     const int src = (kl == 31) ? 0 : kl + 1;
                     const int nb = (kl == 31) ? __shfl_sync(FULL, ntb, src) : __shfl_sync(FULL, ctb, src);
                     const int ne = (kl == 31) ? __shfl_sync(FULL, nte, src) : __shfl_sync(FULL, cte, src);
-                    load_slots(P, F, nb, ne, lane, ncol, nval);
+                    load_slots<T>(P, F, nb, ne, lane, ncol, nval);
                 }
                 // dependency values: inside the task from shared memory, else polled
                 unsigned needm = 0;
@@ -643,7 +665,7 @@ __device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg 
                 for (int t0 = tb + 32 * SJ; t0 < te; t0 += 32 * SJ) {
                     int bc[SJ];
                     T bv[SJ], bx[SJ];
-                    load_slots(P, F, t0, te, lane, bc, bv);
+                    load_slots<T>(P, F, t0, te, lane, bc, bv);
                     unsigned bneed = 0;
     #pragma unroll
                     for (int j = 0; j < SJ; j++) {
@@ -721,6 +743,7 @@ __device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg 
 constexpr int CB = 32;
 constexpr int TS = CB + 1;
 constexpr int CHAIN_MIN = 24;     // shortest task given a CTA
+constexpr int QCHAIN_MAX = 48;    // CTA tasks of a queue's solves
 constexpr int ZCAP_MAX = 8192;    // rows of a CTA task cached in shared memory
 constexpr size_t CHAIN_SMEM = 200 * 1024;   // shared-memory budget of a CTA task
 constexpr int SWARPS = 16;        // warps per CTA of the single-system solves
@@ -737,7 +760,7 @@ __host__ __device__ constexpr size_t chain_smem_bytes(int zcap, size_t tsz) {
 
 template <typename T, bool BACKWARD, bool TRANS>
 __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
-                                               int lo, int hi, const T *__restrict__ F,
+                                               int cidx, int lo, int hi, const T *__restrict__ F,
                                                const T *__restrict__ rcp, const double *__restrict__ rhs,
                                                const double *__restrict__ sp, const T *__restrict__ yin,
                                                T *yout, double *__restrict__ out, int accumulate,
@@ -753,7 +776,7 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
     T *sub = red + CB * TS;                    // [4][CB]: partial sums of 8 lanes each
     T *zs = sub + 4 * CB;                      // [zcap]: results of this task by step
     const int zcap = tk.zcap;
-    const T *tiles = reinterpret_cast<const T *>(tk.tiles) + (size_t)tk.chain_blk0[blockIdx.x] * 2 * CB * CB;
+    const T *tiles = reinterpret_cast<const T *>(tk.tiles) + (size_t)tk.chain_blk0[cidx] * 2 * CB * CB;
     T *mb = zs + zcap;                          // [zcap]: right-hand side term by step
     T *ms = mb + zcap;                          // [zcap]: pivot scale (1 without division)
     int4 *mi = reinterpret_cast<int4 *>(ms + zcap);   // [zcap]: slot bounds (see meta)
@@ -1058,6 +1081,58 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
     }
 }
 
+// A pack of up to 32 single-row tasks (leaves of the elimination tree), a
+// lane per row: forward phases have nothing to wait for (a leaf has no
+// descendants), backward phases wait per lane on the row's ancestors.
+template <typename T, bool BACKWARD, bool TRANS>
+__device__ __forceinline__ void trisolve_pack(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
+                                              const T *__restrict__ F, const T *__restrict__ rcp,
+                                              const double *__restrict__ rhs, const double *__restrict__ sp,
+                                              const T *__restrict__ yin, T *yout, double *__restrict__ out,
+                                              int accumulate, int pk, int lane) {
+    constexpr bool DIV = (TRANS != BACKWARD);
+    const int i = tk.pack_rows[32 * pk + lane];
+    if (i < 0) return;
+    const int dg = P.diag[i];
+    const int tb = BACKWARD ? dg + 1 : P.lu_rp[i];
+    const int te = BACKWARD ? P.lu_rp[i + 1] : dg;
+    const T base = BACKWARD ? yin[i] : (T)(sp[i] * rhs[P.perm[i]]);
+    const T sc = DIV ? rcp[i] : T(1);
+    T acc = T(0);
+    constexpr int U = 8;
+    for (int t0 = tb; t0 < te; t0 += U) {
+        int c[U];
+        T f[U], v[U];
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+            c[q] = -1;
+            f[q] = T(0);
+            if (t0 + q < te) {
+                c[q] = P.lu_ci[t0 + q];
+                f[q] = F[t0 + q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; q++) v[q] = c[q] >= 0 ? ld_relaxed_v(yout + c[q]) : T(0);
+#pragma unroll
+        for (int q = 0; q < U; q++) {
+            if (c[q] >= 0 && is_marker(v[q])) v[q] = wait_value(rc, yout + c[q]);
+            acc = fma(f[q], v[q], acc);
+        }
+    }
+    T r = (base - acc) * sc;
+    if (is_marker(r)) {
+        r = T(NAN);
+        atomicExch(rc.status + ST_NONFINITE, 1);
+    }
+    st_relaxed_v(yout + i, r);
+    if (BACKWARD) {
+        const int oo = P.perm[i];
+        const double w = sp[i] * (double)r;
+        out[oo] = accumulate ? out[oo] + w : w;
+    }
+}
+
 // Packs, once per refactorization, the tiles the CTA tasks of the four solve
 // phases read: for every block b of every CTA task, the diag tile (rows of
 // block b, sources in block b) and the late tile (rows of block b + 1, sources
@@ -1119,7 +1194,7 @@ k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T
         const int tid = tk.chain_task[blockIdx.x];
         const int item = tk.ntasks + blockIdx.x;
         if (wid == 0) trace_mark(rc, tbase, item, 0, lane);
-        trisolve_chain<T, BACKWARD, TRANS>(P, rc, tk, tk.task_lo[tid], tk.task_hi[tid], F, rcp, rhs, sp,
+        trisolve_chain<T, BACKWARD, TRANS>(P, rc, tk, blockIdx.x, tk.task_lo[tid], tk.task_hi[tid], F, rcp, rhs, sp,
                                            yin, yout, out, accumulate, smem);
         if (wid == 0) trace_mark(rc, tbase, item, 1, lane);
         if (lane == 0) finish_launch(rc, e);
@@ -1131,8 +1206,13 @@ k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T
         const int slot = claim_row(rc, lane);
         if (slot >= tk.ntasks) break;
         trace_mark(rc, tbase, slot, 0, lane);
-        trisolve_task<T, BACKWARD, TRANS>(P, rc, tk, F, rcp, rhs, sp, yin, yout, out, accumulate,
-                                          order[slot], loc, lane);
+        const int tid = order[slot];
+        if (tid < 0)
+            trisolve_pack<T, BACKWARD, TRANS>(P, rc, tk, F, rcp, rhs, sp, yin, yout, out, accumulate, -1 - tid,
+                                              lane);
+        else
+            trisolve_task<T, BACKWARD, TRANS>(P, rc, tk, F, rcp, rhs, sp, yin, yout, out, accumulate, tid, loc,
+                                              lane);
         trace_mark(rc, tbase, slot, 1, lane);
     }
     if (lane == 0) finish_launch(rc, e);
@@ -1258,12 +1338,12 @@ __global__ void k_vscale(double *__restrict__ v, const double *__restrict__ w, d
 
 // ===========================================================================
 // Batched same-pattern systems (batch innermost): value k of system s sits at
-// k * B + s, vector entry i of system s at i * B + s.  One warp handles one
-// row (refactorization) or one task (solves) for 32 systems, one system per
-// lane; every lane runs its system's elimination sequentially, so an FP64
-// instruction serves 32 systems and every access is coalesced across the
-// batch.  Work items are (row or task, group of 32 systems), claimed in
-// topological order.
+// k * B + s, vector entry i of system s at i * B + s.  Work items are (row or
+// task, system), claimed in topological order with every system of a row or
+// task together; each item runs the single-system body (a warp per row or
+// task of one system, the row's columns across the lanes) through Strided
+// accessors.  The B systems' independent dependency chains run side by side,
+// so the batch fills the GPU that one latency-bound system leaves idle.
 
 __device__ __forceinline__ double ld_acquire_v(const double *p) {
     double v;
@@ -1356,90 +1436,28 @@ __global__ void k_bamax(DevPattern P, int B, const double *__restrict__ aval, co
     if (isfinite(csum)) atomic_max_nonneg(norms + (long long)NM_A1NORM * B + sy, csum);
 }
 
+// Batched refactorization: work items (row, system), rows deepest first and
+// every system of a row together; each item is the single-system row body on
+// that system's batch-innermost arrays (a warp per row of one system, its
+// columns across the lanes).
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32, 2)
 k_brefactor(DevPattern P, RunCfg rc, int B, const double *__restrict__ aval, const double *__restrict__ sp,
             const unsigned long long *__restrict__ norms, T *LU, T *LUT, T *rcp, double tau_rel) {
-    const int lane = threadIdx.x & 31;
-    const int G = (B + 31) >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *sval = reinterpret_cast<T *>(smem) + (size_t)wid * rc.cap;
+    int *scol = reinterpret_cast<int *>(smem + (size_t)nw * rc.cap * sizeof(T)) + (size_t)wid * rc.cap;
     const int e = rc.sched->epoch + 1;
-    const bool mapped = P.upd_off != nullptr;
+    const int gw = blockIdx.x * nw + wid;
     for (;;) {
         const int slot = claim_row(rc, lane);
-        if (slot >= P.n * G) break;
-        const int i = P.order_f[slot / G];
-        const int sy = (slot % G) * 32 + lane;
-        const bool act = sy < B;
-        const int sy_ = act ? sy : 0;
-        const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
-        const double si = sp[(long long)i * B + sy_];
-        const double tau = tau_rel * __longlong_as_double((long long)norms[(long long)NM_AMAX * B + sy_]);
-        T *w = LU + (long long)rb * B + sy_;                 // this system's row, stride B
-        for (int t = 0; t < len; t++) {
-            const int k = P.src[rb + t];
-            const double v = (k >= 0 && act) ? si * sp[(long long)P.lu_ci[rb + t] * B + sy_] *
-                                                   aval[(long long)k * B + sy_]
-                                             : 0.0;
-            if (act) w[(long long)t * B] = (T)v;
-        }
-        for (int t = 0; t < dp; t++) {
-            const int d = P.lu_ci[rb + t];
-            const int ub = P.diag[d], ue = P.lu_rp[d + 1];
-            const unsigned mo = mapped ? P.upd_off[rb + t] : 0u;
-            const T r = warp_wait_acquire(rc, rcp + (long long)d * B + sy_, act, lane);
-            if (!act) continue;
-            const T l = w[(long long)t * B] * r;
-            const T *ud = LU + sy_;
-            // the targets of one pivot step are distinct: eight updates at a
-            // time, all loads issued before the stores (memory-level parallelism)
-            for (int u0 = ub + 1; u0 < ue; u0 += 8) {
-                int lo[8];
-                T a[8], x[8];
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const int u = u0 + q;
-                    lo[q] = -1;
-                    if (u < ue) {
-                        if (mapped) {
-                            lo[q] = P.upd_map[mo + (u - ub - 1)];
-                        } else {
-                            const int j = P.lu_ci[u];
-                            int a_ = t + 1, b_ = len;
-                            while (a_ < b_) {
-                                const int mid = (a_ + b_) >> 1;
-                                if (P.lu_ci[rb + mid] < j) a_ = mid + 1; else b_ = mid;
-                            }
-                            if (a_ < len && P.lu_ci[rb + a_] == j) lo[q] = a_;
-                            else atomicExch(rc.status + ST_INTERNAL, 1);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    a[q] = lo[q] >= 0 ? ud[(long long)(u0 + q) * B] : T(0);
-                    x[q] = lo[q] >= 0 ? w[(long long)lo[q] * B] : T(0);
-                }
-#pragma unroll
-                for (int q = 0; q < 8; q++)
-                    if (lo[q] >= 0) w[(long long)lo[q] * B] = x[q] - l * a[q];
-            }
-            w[(long long)t * B] = l;
-        }
-        if (act) {
-            double pv = (double)w[(long long)dp * B];
-            if (!(fabs(pv) >= tau) || isinf(pv)) {
-                const int k = P.src[rb + dp];
-                const double aii = (k >= 0) ? si * si * aval[(long long)k * B + sy_] : 0.0;
-                if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
-                pv = (aii < 0.0) ? -tau : tau;
-                atomicAdd(rc.status + ST_PERTURBED, 1);
-            }
-            w[(long long)dp * B] = (T)pv;
-            for (int t = 0; t < len; t++) LUT[(long long)P.tpos[rb + t] * B + sy_] = w[(long long)t * B];
-            T rv = T(1) / (T)pv;
-            if (is_marker(rv)) rv = T(NAN);
-            st_release_v(rcp + (long long)i * B + sy_, rv);   // orders this lane's row stores before it
-        }
+        if (slot >= P.n * B) break;
+        const int i = P.order_f[slot / B], sy = slot % B;
+        const double tau = tau_rel * __longlong_as_double((long long)norms[(long long)NM_AMAX * B + sy]);
+        refactor_row<T>(P, rc, Strided<const double>{aval, B, sy}, Strided<const double>{sp, B, sy},
+                        Strided<T>{LU, B, sy}, Strided<T>{LUT, B, sy}, Strided<T>{rcp, B, sy}, tau, i, sval,
+                        scol, gw, lane);
     }
     if (lane == 0) finish_launch(rc, e);
 }
@@ -1450,70 +1468,19 @@ __global__ void __launch_bounds__(WARPS * 32, 2)
 k_btrisolve(DevPattern P, RunCfg rc, TaskCfg tk, int B, const T *__restrict__ F, const T *__restrict__ rcp,
             const double *__restrict__ rhs, const double *__restrict__ sp, const T *__restrict__ yin, T *yout,
             double *__restrict__ out, int accumulate) {
-    const int lane = threadIdx.x & 31;
-    const int G = (B + 31) >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T *loc = reinterpret_cast<T *>(smem) + (size_t)wid * tk.cap;
     const int e = rc.sched->epoch + 1;
     const int *order = BACKWARD ? tk.order_b : tk.order_topo;
-    constexpr bool DIV = (TRANS != BACKWARD);
     for (;;) {
         const int slot = claim_row(rc, lane);
-        if (slot >= tk.ntasks * G) break;
-        const int tid = order[slot / G];
-        const int sy = (slot % G) * 32 + lane;
-        const bool act = sy < B;
-        const int sy_ = act ? sy : 0;
-        const int lo = tk.task_lo[tid], hi = tk.task_hi[tid];
-        const int m = hi - lo + 1;
-        for (int k = 0; k < m; k++) {
-            const int i = BACKWARD ? hi - k : lo + k;
-            const int dg = P.diag[i];
-            const int tb = BACKWARD ? dg + 1 : P.lu_rp[i];
-            const int te = BACKWARD ? P.lu_rp[i + 1] : dg;
-            T acc = 0;
-            for (int t0 = tb; t0 < te; t0 += 8) {
-                T a[8], v[8];
-                int c[8];
-                unsigned need = 0;
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const int t = t0 + q;
-                    a[q] = T(0);
-                    v[q] = T(0);
-                    c[q] = 0;
-                    if (t < te) {
-                        c[q] = P.lu_ci[t];
-                        a[q] = F[(long long)t * B + sy_];
-                        v[q] = ld_relaxed_v(yout + (long long)c[q] * B + sy_);
-                        if (act && is_marker(v[q])) need |= 1u << q;
-                    }
-                }
-                if (__any_sync(FULL, need != 0)) {
-#pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        const bool nq = (need >> q) & 1u;
-                        const T w = warp_wait_load(rc, yout + (long long)c[q] * B + sy_, nq, lane);
-                        if (nq) v[q] = w;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 8; q++) acc += a[q] * v[q];
-            }
-            if (act) {
-                T r = (BACKWARD ? yin[(long long)i * B + sy] : (T)(sp[(long long)i * B + sy] *
-                                                                   rhs[(long long)P.perm[i] * B + sy])) - acc;
-                if (DIV) r = r * rcp[(long long)i * B + sy];
-                if (is_marker(r)) {
-                    r = T(NAN);
-                    atomicExch(rc.status + ST_NONFINITE, 1);
-                }
-                st_relaxed_v(yout + (long long)i * B + sy, r);
-                if (BACKWARD) {
-                    const long long o = (long long)P.perm[i] * B + sy;
-                    const double w = sp[(long long)i * B + sy] * (double)r;
-                    out[o] = accumulate ? out[o] + w : w;
-                }
-            }
-        }
+        if (slot >= tk.ntasks * B) break;
+        const int tid = order[slot / B], sy = slot % B;
+        trisolve_task<T, BACKWARD, TRANS>(P, rc, tk, Strided<const T>{F, B, sy}, Strided<const T>{rcp, B, sy},
+                                          Strided<const double>{rhs, B, sy}, Strided<const double>{sp, B, sy},
+                                          Strided<const T>{yin, B, sy}, Strided<T>{yout, B, sy},
+                                          Strided<double>{out, B, sy}, accumulate, tid, loc, lane);
     }
     if (lane == 0) finish_launch(rc, e);
 }
@@ -1527,6 +1494,7 @@ k_btrisolve(DevPattern P, RunCfg rc, TaskCfg tk, int B, const T *__restrict__ F,
 struct QSys {
     DevPattern P;
     TaskCfg tk;
+    TaskCfg tkc[4];                    // CTA tasks of each solve phase (forward, backward, transposed)
     void *LU, *LUT, *rcp, *y;          // factor, transposed factor, reciprocal pivots, 2n work
     const double *sp;                  // scaling in permuted order
     const unsigned long long *norms;   // the context's norm words (NM_AMAX for tau)
@@ -1564,10 +1532,28 @@ k_qrefactor(const QSys *__restrict__ sys, const int2 *__restrict__ items, int ni
 template <typename T, bool BACKWARD, bool TRANS>
 __global__ void __launch_bounds__(WARPS * 32, 2)
 k_qtrisolve(const QSys *__restrict__ sys, const int2 *__restrict__ items, int nitems, RunCfg rc, int refine,
-            int tcap) {
+            int tcap, const int2 *__restrict__ chains, int nch) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int e = rc.sched->epoch + 1;
+    if ((int)blockIdx.x < nch) {            // a long task of one system on this whole CTA
+        const int2 ch = chains[blockIdx.x];
+        const QSys &q = sys[ch.x];
+        const TaskCfg &tk = q.tkc[(TRANS ? 2 : 0) + (BACKWARD ? 1 : 0)];
+        const int tid = tk.chain_task[ch.y];
+        T *y = (T *)q.y, *z = y + q.n;
+        const T *F = (const T *)(TRANS ? q.LUT : q.LU);
+        if (BACKWARD)
+            trisolve_chain<T, true, TRANS>(q.P, rc, tk, ch.y, tk.task_lo[tid], tk.task_hi[tid], F,
+                                           (const T *)q.rcp, nullptr, q.sp, y, z, TRANS ? q.lam : q.x,
+                                           TRANS ? 0 : refine, smem);
+        else
+            trisolve_chain<T, false, TRANS>(q.P, rc, tk, ch.y, tk.task_lo[tid], tk.task_hi[tid], F,
+                                            (const T *)q.rcp, TRANS ? q.g : (refine ? q.rho : q.b), q.sp,
+                                            nullptr, y, nullptr, 0, smem);
+        if (lane == 0) finish_launch(rc, e);
+        return;
+    }
     // per-warp slice of the queue-wide capacity (at least every system's tk.cap)
     T *loc = reinterpret_cast<T *>(smem) + (size_t)wid * tcap;
     for (;;) {
@@ -1580,11 +1566,11 @@ k_qtrisolve(const QSys *__restrict__ sys, const int2 *__restrict__ items, int ni
         const double *rhs = TRANS ? q.g : (refine ? q.rho : q.b);
         double *out = TRANS ? q.lam : q.x;
         if (BACKWARD)
-            trisolve_task<T, true, TRANS>(q.P, rc, q.tk, F, (const T *)q.rcp, nullptr, q.sp, y, z, out,
-                                          TRANS ? 0 : refine, it.y, loc, lane);
+            trisolve_task<T, true, TRANS>(q.P, rc, q.tk, F, (const T *)q.rcp, (const double *)nullptr, q.sp,
+                                          (const T *)y, z, out, TRANS ? 0 : refine, it.y, loc, lane);
         else
-            trisolve_task<T, false, TRANS>(q.P, rc, q.tk, F, (const T *)q.rcp, rhs, q.sp, nullptr, y, nullptr, 0,
-                                           it.y, loc, lane);
+            trisolve_task<T, false, TRANS>(q.P, rc, q.tk, F, (const T *)q.rcp, rhs, q.sp, (const T *)nullptr, y,
+                                           (double *)nullptr, 0, it.y, loc, lane);
     }
     if (lane == 0) finish_launch(rc, e);
 }
@@ -1693,7 +1679,8 @@ struct kkt_ctx {
     int nblk = 0;                    // blocks of all CTA tasks
     void *d_tiles = nullptr;         // packed tiles, 4 phases x nblk x 2 x 32 x 32
     bool tiles_fresh = false;        // d_tiles match the current factors
-    size_t solve_smem = 0;
+    std::vector<int> chain_h;        // CTA tasks of the single-system solves (host copy)
+    size_t solve_smem = 0, bsolve_smem = 0;
     unsigned long long *h_norms = nullptr;  // pinned
     int grid = 0, solve_grid = 0, bsolve_grid = 0, cta_warps = WARPS, solve_warps = SWARPS, cap = 0;
     size_t smem = 0, device_bytes = 0;
@@ -1903,7 +1890,7 @@ static kkt_status upload(kkt_ctx *c) {
         // tasks); backward = by height of the top row, from the root;
         // topological = deepest top rows first.
         auto orders = [&](const std::vector<int> &set, long long warps, std::vector<int> &of,
-                          std::vector<int> &ob, std::vector<int> &ot) {
+                          std::vector<int> &ob, std::vector<int> &ot, long long *nlong = nullptr) {
             std::vector<int> bylen(set);
             std::sort(bylen.begin(), bylen.end(), [&](int x, int y) { return len[x] > len[y]; });
             const long long max_long = std::max(0LL, warps / 4);
@@ -1918,6 +1905,7 @@ static kkt_status upload(kkt_ctx *c) {
                 lmin = len[bylen[q]];
                 q = r;
             }
+            if (nlong) *nlong = cnt;
             of = set;
             ob = set;
             ot = set;
@@ -1953,7 +1941,30 @@ static kkt_status upload(kkt_ctx *c) {
                 if (!is_chain[T]) reg.push_back(T);
         }
         std::vector<int> of1, ob1, ot1;
-        orders(reg, (long long)(c->solve_grid - (int)chain.size()) * snw, of1, ob1, ot1);
+        long long nlong1 = 0;
+        orders(reg, (long long)(c->solve_grid - (int)chain.size()) * snw, of1, ob1, ot1, &nlong1);
+        // Single-row tasks (leaves of the tree) in packs of 32, a lane per row:
+        // forward they depend on nothing and follow the longest-first prefix;
+        // backward they depend only on ancestors and come last.  An order entry
+        // p < 0 stands for pack -1 - p.
+        std::vector<int> pack_rows;
+        {
+            std::vector<int> leaves, f2, b2;
+            for (int T : of1)
+                if (len[T] == 1) leaves.push_back(T);
+            const int npk = (int)((leaves.size() + 31) / 32);
+            pack_rows.assign((size_t)npk * 32, -1);
+            for (size_t q = 0; q < leaves.size(); q++) pack_rows[q] = a.task_lo[leaves[q]];
+            for (long long q = 0; q < nlong1; q++) f2.push_back(of1[q]);
+            for (int p = 0; p < npk; p++) f2.push_back(-1 - p);
+            for (size_t q = (size_t)nlong1; q < of1.size(); q++)
+                if (len[of1[q]] > 1) f2.push_back(of1[q]);
+            for (int T : ob1)
+                if (len[T] > 1) b2.push_back(T);
+            for (int p = 0; p < npk; p++) b2.push_back(-1 - p);
+            of1.swap(f2);
+            ob1.swap(b2);
+        }
         // blocks of the CTA tasks (for the packed tiles)
         std::vector<int> blk0(chain.size() + 1, 0), binfo;
         for (size_t q = 0; q < chain.size(); q++) {
@@ -1997,7 +2008,7 @@ static kkt_status upload(kkt_ctx *c) {
         }
         int *d = nullptr;
         const size_t words = 3 * (size_t)nt + 3 * (size_t)nt + chain.size() + 4 * (size_t)n + blk0.size() +
-                             binfo.size();
+                             binfo.size() + pack_rows.size();
         CK(cudaMalloc(&d, words * sizeof(int)));
         size_t o = 0;
         auto put = [&](const std::vector<int> &v) -> const int * {
@@ -2016,13 +2027,15 @@ static kkt_status upload(kkt_ctx *c) {
         c->tk.order_topo = put(ot);
         c->tk1.task_lo = c->tk.task_lo;
         c->tk1.task_hi = c->tk.task_hi;
-        c->tk1.ntasks = (int)reg.size();
+        c->tk1.ntasks = (int)of1.size();
         c->tk1.order_f = put(of1);
         c->tk1.order_b = put(ob1);
         c->tk1.order_topo = put(ot1);
         c->tk1.nchain = (int)chain.size();
         c->tk1.chain_task = put(chain);
+        c->chain_h = chain;
         c->tk1.chain_blk0 = put(blk0);
+        c->tk1.pack_rows = put(pack_rows);
         c->blk_info = put(binfo);
         c->nblk = blk0.back();
         c->cs_fwd = put(std::vector<int>(csl.begin(), csl.begin() + n));
@@ -2098,11 +2111,30 @@ static kkt_status upload(kkt_ctx *c) {
         CK(cudaMalloc(&c->b_norms, NM_WORDS * Bc * sizeof(unsigned long long)));
         CK(cudaMallocHost(&c->hb_norms, NM_WORDS * Bc * sizeof(unsigned long long)));
         c->device_bytes += (2 * nlu + 3 * (size_t)n) * Bc * tsz + 3 * (size_t)n * Bc * sizeof(double);
+        c->bsolve_smem = (size_t)nw * c->tk.cap * tsz;
+        auto setb = [&](const void *f, size_t bytes) {
+            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        };
         if (f32) {
-            CK(cudaFuncSetAttribute(k_brefactor<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+            CK(setb((const void *)k_brefactor<float>, c->smem));
+            CK(setb((const void *)k_btrisolve<float, false, false>, c->bsolve_smem));
+            CK(setb((const void *)k_btrisolve<float, true, false>, c->bsolve_smem));
+            CK(setb((const void *)k_btrisolve<float, false, true>, c->bsolve_smem));
+            CK(setb((const void *)k_btrisolve<float, true, true>, c->bsolve_smem));
         } else {
-            CK(cudaFuncSetAttribute(k_brefactor<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+            CK(setb((const void *)k_brefactor<double>, c->smem));
+            CK(setb((const void *)k_btrisolve<double, false, false>, c->bsolve_smem));
+            CK(setb((const void *)k_btrisolve<double, true, false>, c->bsolve_smem));
+            CK(setb((const void *)k_btrisolve<double, false, true>, c->bsolve_smem));
+            CK(setb((const void *)k_btrisolve<double, true, true>, c->bsolve_smem));
         }
+        // every CTA of a batched solve must be resident at once (waiting warps)
+        int per_sm_b = 0;
+        if (f32) CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_btrisolve<float, false, false>,
+                                                                  nw * 32, c->bsolve_smem));
+        else CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_btrisolve<double, false, false>,
+                                                              nw * 32, c->bsolve_smem));
+        if ((long long)per_sm_b * sms < c->bsolve_grid) c->bsolve_grid = per_sm_b * sms;
     }
     if (c->opt.trace) {
         const long long items = std::max<long long>(n, c->tk.ntasks);
@@ -2568,8 +2600,10 @@ static void ensure_view(const kkt_ctx *c);
 
 template <typename T> static kkt_status launch_brefactor(kkt_ctx *c, int B, cudaStream_t s) {
     const int n = c->an.n;
+    // every entry starts as the not-ready marker; published entries overwrite it
+    CK(cudaMemsetAsync(c->b_lu, 0xff, (size_t)c->nnz_lu * B * sizeof(T), s));
     CK(cudaMemsetAsync(c->b_rcp, 0xff, (size_t)n * B * sizeof(T), s));
-    k_brefactor<T><<<c->grid, c->cta_warps * 32, 0, s>>>(c->P, c->rc, B, c->b_values, c->b_sp, c->b_norms,
+    k_brefactor<T><<<c->grid, c->cta_warps * 32, c->smem, s>>>(c->P, c->rc, B, c->b_values, c->b_sp, c->b_norms,
                                                           (T *)c->b_lu, (T *)c->b_lut, (T *)c->b_rcp, c->tau_rel);
     CK(cudaGetLastError());
     c->launches++;
@@ -2604,18 +2638,18 @@ static kkt_status launch_bsolve(kkt_ctx *c, int B, const double *b, double *x, i
     const T *F = (const T *)(transpose ? c->b_lut : c->b_lu), *R = (const T *)c->b_rcp;
     CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * B * sizeof(T), s));
     if (transpose) {
-        k_btrisolve<T, false, true><<<c->bsolve_grid, c->cta_warps * 32, 0, s>>>(
+        k_btrisolve<T, false, true><<<c->bsolve_grid, c->cta_warps * 32, c->bsolve_smem, s>>>(
             c->P, c->rc, c->tk, B, F, R, b, c->b_sp, nullptr, y, nullptr, 0);
         CK(cudaGetLastError());
         c->launches++;
-        k_btrisolve<T, true, true><<<c->bsolve_grid, c->cta_warps * 32, 0, s>>>(
+        k_btrisolve<T, true, true><<<c->bsolve_grid, c->cta_warps * 32, c->bsolve_smem, s>>>(
             c->P, c->rc, c->tk, B, F, R, nullptr, c->b_sp, y, z, x, accumulate);
     } else {
-        k_btrisolve<T, false, false><<<c->bsolve_grid, c->cta_warps * 32, 0, s>>>(
+        k_btrisolve<T, false, false><<<c->bsolve_grid, c->cta_warps * 32, c->bsolve_smem, s>>>(
             c->P, c->rc, c->tk, B, F, R, b, c->b_sp, nullptr, y, nullptr, 0);
         CK(cudaGetLastError());
         c->launches++;
-        k_btrisolve<T, true, false><<<c->bsolve_grid, c->cta_warps * 32, 0, s>>>(
+        k_btrisolve<T, true, false><<<c->bsolve_grid, c->cta_warps * 32, c->bsolve_smem, s>>>(
             c->P, c->rc, c->tk, B, F, R, nullptr, c->b_sp, y, z, x, accumulate);
     }
     CK(cudaGetLastError());
@@ -2752,6 +2786,12 @@ struct kkt_queue {
     std::vector<QSys> h_sys;
     int2 *d_items = nullptr;          // refactor | forward | backward items
     int n_ref = 0, n_fwd = 0, n_bwd = 0;
+    // With CTAs of WARPS warps the solves run the longest tasks (from the
+    // contexts' CTA tasks) on a CTA each: d_chains (system, chain index), and
+    // d_items_reg the forward | backward items without them.
+    int nch = 0, n_fwd_reg = 0, n_bwd_reg = 0;
+    int2 *d_chains = nullptr, *d_items_reg = nullptr;
+    size_t smem_chain = 0;
     Sched *d_sched = nullptr;
     int *d_status = nullptr;
     void *d_scratch = nullptr;
@@ -2778,6 +2818,7 @@ static kkt_status q_configure(kkt_queue *q, int cta_warps, int ctas) {
     const int nw = q->cta_warps;
     q->smem_ref = (size_t)nw * q->cap * (tsz + sizeof(int));
     q->smem_sol = (size_t)nw * q->tcap * tsz;
+    if (nw == WARPS && q->nch > 0) q->smem_sol = std::max(q->smem_sol, q->smem_chain);
     kkt_status st = q->f32 ? q_set_smem<float>(q) : q_set_smem<double>(q);
     if (st) return st;
     int sms = 0, per_sm = 0;
@@ -2829,14 +2870,17 @@ kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
     q->dev = ctxs[0]->dev;
     q->f32 = ctxs[0]->opt.factor_fp32 != 0;
     DeviceGuard g(q->dev);
-    // items: refactor rows by (level, system, position); solve tasks by top level
+    // items: refactor rows deepest first (by distance to the root, across
+    // systems), forward solve tasks by depth of their top row, deepest first;
+    // backward solve tasks by height of their top row, from the root (each a
+    // topological order of every system; see the single-system claim orders)
     std::vector<std::array<int, 4>> ref, fwd, bwd;
     for (int k = 0; k < m; k++) {
         const Analysis &a = q->ctx[k]->an;
-        for (int r = 0; r < a.n; r++) ref.push_back({a.level[a.order_f[r]], k, r, a.order_f[r]});
+        for (int r = 0; r < a.n; r++) ref.push_back({-a.level_u[a.order_f[r]], k, r, a.order_f[r]});
         for (int t = 0; t < (int)a.task_lo.size(); t++) {
             const int top = a.level[a.task_hi[t]];
-            fwd.push_back({top, k, t, t});
+            fwd.push_back({-a.level_u[a.task_hi[t]], k, t, t});
             bwd.push_back({-top, k, t, t});
         }
         q->cap = std::max(q->cap, q->ctx[k]->cap);
@@ -2854,6 +2898,44 @@ kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
     q->n_bwd = (int)bwd.size();
     CK(cudaMalloc(&q->d_items, items.size() * sizeof(int2)));
     CK(cudaMemcpy(q->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    {   // CTA tasks: the longest of the contexts' CTA tasks, at most QCHAIN_MAX
+        std::vector<std::array<int, 3>> cand;          // (length, system, chain index)
+        for (int k = 0; k < m; k++) {
+            const kkt_ctx *c = q->ctx[k];
+            for (int ci = 0; ci < (int)c->chain_h.size(); ci++) {
+                const int T = c->chain_h[ci];
+                cand.push_back({c->an.task_hi[T] - c->an.task_lo[T] + 1, k, ci});
+            }
+        }
+        std::stable_sort(cand.begin(), cand.end(), [](const std::array<int, 3> &x, const std::array<int, 3> &y) {
+            return x[0] > y[0];
+        });
+        if ((int)cand.size() > QCHAIN_MAX) cand.resize(QCHAIN_MAX);
+        std::vector<int2> chains;
+        std::set<std::pair<int, int>> taken;           // (system, task)
+        const size_t tsz = q->f32 ? sizeof(float) : sizeof(double);
+        for (auto &cd : cand) {
+            const kkt_ctx *c = q->ctx[cd[1]];
+            chains.push_back(make_int2(cd[1], cd[2]));
+            taken.insert({cd[1], c->chain_h[cd[2]]});
+            q->smem_chain = std::max(q->smem_chain, chain_smem_bytes(c->tk1.zcap, tsz));
+        }
+        std::vector<int2> reg;
+        for (auto &v : fwd)
+            if (!taken.count({v[1], v[3]})) reg.push_back(make_int2(v[1], v[3]));
+        q->n_fwd_reg = (int)reg.size();
+        for (auto &v : bwd)
+            if (!taken.count({v[1], v[3]})) reg.push_back(make_int2(v[1], v[3]));
+        q->n_bwd_reg = (int)reg.size() - q->n_fwd_reg;
+        q->nch = (int)chains.size();
+        if (q->nch > 0) {
+            CK(cudaMalloc(&q->d_chains, chains.size() * sizeof(int2)));
+            CK(cudaMemcpy(q->d_chains, chains.data(), chains.size() * sizeof(int2), cudaMemcpyHostToDevice));
+            CK(cudaMalloc(&q->d_items_reg, std::max<size_t>(1, reg.size()) * sizeof(int2)));
+            if (!reg.empty())
+                CK(cudaMemcpy(q->d_items_reg, reg.data(), reg.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        }
+    }
     CK(cudaMalloc(&q->d_sys, m * sizeof(QSys)));
     CK(cudaMalloc(&q->d_sched, sizeof(Sched)));
     CK(cudaMemset(q->d_sched, 0, sizeof(Sched)));
@@ -2875,6 +2957,7 @@ kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
         s.rho = c->d_rho;
         s.tau_rel = c->tau_rel;
         s.n = c->an.n;
+        for (int ph = 0; ph < 4; ph++) s.tkc[ph] = tasks_of(c, ph & 1, ph >= 2);
     }
     q->rc = ctxs[0]->rc;
     q->rc.status = q->d_status;
@@ -2892,6 +2975,8 @@ void kkt_queue_destroy(kkt_queue *q) {
     DeviceGuard g(q->dev);
     if (q->graph) cudaGraphExecDestroy(q->graph);
     cudaFree(q->d_items);
+    cudaFree(q->d_chains);
+    cudaFree(q->d_items_reg);
     cudaFree(q->d_sys);
     cudaFree(q->d_sched);
     cudaFree(q->d_status);
@@ -2926,6 +3011,21 @@ static kkt_status q_record(kkt_queue *q, int n_refine, double *omega_dev, cudaSt
     k_qrefactor<T><<<q->grid, nw * 32, q->smem_ref, s>>>(q->d_sys, ir, q->n_ref, q->rc);
     CK(cudaGetLastError());
     q->launches++;
+    // tiles of the contexts' CTA tasks from the new factors
+    for (int k = 0; k < q->m; k++) {
+        kkt_ctx *c = q->ctx[k];
+        if (c->nblk == 0) continue;
+        const long long threads = 4LL * c->nblk * 2 * CB * 32;
+        k_pack_tiles<T><<<blocks_for(threads, 256), 256, 0, s>>>(
+            c->P, c->blk_info, c->nblk, c->cs_fwd, c->csd_fwd, c->cs_bwd, c->csd_bwd, (const T *)c->d_lu,
+            (const T *)c->d_lut, (const T *)c->d_rcp, (T *)c->d_tiles);
+        CK(cudaGetLastError());
+        q->launches++;
+    }
+    const bool cta = (nw == WARPS && q->nch > 0);
+    const int nch = cta ? q->nch : 0;
+    const int2 *sf = cta ? q->d_items_reg : iff, *sb = cta ? q->d_items_reg + q->n_fwd_reg : ib;
+    const int nf = cta ? q->n_fwd_reg : q->n_fwd, nbk = cta ? q->n_bwd_reg : q->n_bwd;
     for (int pass = 0; pass <= n_refine; pass++) {
         if (pass > 0) {
             for (int k = 0; k < q->m; k++) {
@@ -2940,9 +3040,11 @@ static kkt_status q_record(kkt_queue *q, int n_refine, double *omega_dev, cudaSt
         }
         for (int k = 0; k < q->m; k++)
             CK(cudaMemsetAsync(q->ctx[k]->d_y, 0xff, 2 * (size_t)q->ctx[k]->an.n * sizeof(T), s));
-        k_qtrisolve<T, false, false><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, iff, q->n_fwd, q->rc, pass > 0, q->tcap);
+        k_qtrisolve<T, false, false><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, sf, nf, q->rc, pass > 0,
+                                                                            q->tcap, q->d_chains, nch);
         CK(cudaGetLastError());
-        k_qtrisolve<T, true, false><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, ib, q->n_bwd, q->rc, pass > 0, q->tcap);
+        k_qtrisolve<T, true, false><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, sb, nbk, q->rc, pass > 0,
+                                                                           q->tcap, q->d_chains, nch);
         CK(cudaGetLastError());
         q->launches += 2;
     }
@@ -2999,12 +3101,11 @@ kkt_status kkt_queue_run(kkt_queue *q, const double *const *values, const double
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
         q->key = key;
     }
-    // every run writes new factors: the contexts' packed tiles are stale until
-    // their next single-system solve packs them again
+    // every run writes new factors and packs the contexts' tiles from them
     for (int k = 0; k < q->m; k++) {
         q->ctx[k]->values = values[k];
         q->ctx[k]->factored = true;
-        q->ctx[k]->tiles_fresh = false;
+        q->ctx[k]->tiles_fresh = true;
     }
     CK(cudaGraphLaunch(q->graph, s));
     return KKT_OK;
@@ -3023,17 +3124,30 @@ kkt_status kkt_queue_solve_transpose(kkt_queue *q, const double *const *g_, doub
     CK(cudaMemcpy(q->d_sys, q->h_sys.data(), q->m * sizeof(QSys), cudaMemcpyHostToDevice));
     const int nw = q->cta_warps;
     const int2 *iff = q->d_items + q->n_ref, *ib = iff + q->n_fwd;
-    for (int k = 0; k < q->m; k++)
-        CK(cudaMemsetAsync(q->ctx[k]->d_y, 0xff, 2 * (size_t)q->ctx[k]->an.n *
-                                                  (q->f32 ? sizeof(float) : sizeof(double)), s));
+    for (int k = 0; k < q->m; k++) {
+        kkt_ctx *c = q->ctx[k];
+        if (!c->tiles_fresh) {              // factors of a single-system refactor not yet packed
+            kkt_status r = q->f32 ? pack_tiles<float>(c, s) : pack_tiles<double>(c, s);
+            if (r != KKT_OK) return r;
+        }
+        CK(cudaMemsetAsync(c->d_y, 0xff, 2 * (size_t)c->an.n * (q->f32 ? sizeof(float) : sizeof(double)), s));
+    }
+    const bool cta = (nw == WARPS && q->nch > 0);
+    const int nch = cta ? q->nch : 0;
+    const int2 *sf = cta ? q->d_items_reg : iff, *sb = cta ? q->d_items_reg + q->n_fwd_reg : ib;
+    const int nf = cta ? q->n_fwd_reg : q->n_fwd, nbk = cta ? q->n_bwd_reg : q->n_bwd;
     if (q->f32) {
-        k_qtrisolve<float, false, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, iff, q->n_fwd, q->rc, 0, q->tcap);
+        k_qtrisolve<float, false, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, sf, nf, q->rc, 0, q->tcap,
+                                                                               q->d_chains, nch);
         CK(cudaGetLastError());
-        k_qtrisolve<float, true, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, ib, q->n_bwd, q->rc, 0, q->tcap);
+        k_qtrisolve<float, true, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, sb, nbk, q->rc, 0, q->tcap,
+                                                                              q->d_chains, nch);
     } else {
-        k_qtrisolve<double, false, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, iff, q->n_fwd, q->rc, 0, q->tcap);
+        k_qtrisolve<double, false, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, sf, nf, q->rc, 0, q->tcap,
+                                                                                q->d_chains, nch);
         CK(cudaGetLastError());
-        k_qtrisolve<double, true, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, ib, q->n_bwd, q->rc, 0, q->tcap);
+        k_qtrisolve<double, true, true><<<q->sgrid, nw * 32, q->smem_sol, s>>>(q->d_sys, sb, nbk, q->rc, 0, q->tcap,
+                                                                               q->d_chains, nch);
     }
     CK(cudaGetLastError());
     q->launches += 2;
