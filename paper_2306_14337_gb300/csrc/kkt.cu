@@ -335,7 +335,7 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
             // Pivot steps are pipelined: while step t computes, the reciprocal
             // pivot and the first 32 x UJ entries (targets, values) of step t+1 are
             // already in flight; a value still unpublished is polled again.
-            constexpr int UJ = 4;
+            constexpr int UJ = sizeof(T) == 4 ? 8 : 4;   // FP32 rows hold twice the entries in flight
             int md = 0, mub = 0, mue = 0;       // metadata of steps t0..t0+31, one per lane
             unsigned mmo = 0;
             auto load_meta = [&](int t0) {
