@@ -946,17 +946,19 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
             for (int r = 0; r < ER; r++) gather(r);
 #pragma unroll
             for (int r = 0; r < ER; r++) finish(r);
-            // longer rows: the rest in chunks of 32 x EJ2, the next chunk's
-            // slots in flight while this one's sources are read
+            // longer rows: the rest in chunks of 32 x E2 slots (E2 = 16 for
+            // FP32, 8 for FP64), the next chunk's slots in flight while this
+            // one's sources are read
+            constexpr int E2 = sizeof(T) == 4 ? 2 * EJ2 : EJ2;
 #pragma unroll
             for (int r = 0; r < ER; r++) {
                 int t0 = eb[r] + 32 * EJ;
                 if (t0 >= ee[r]) continue;
-                int c1[EJ2];
-                T f1[EJ2];
-                auto load2 = [&](int tb, int (&c)[EJ2], T (&f)[EJ2]) {
+                int c1[E2];
+                T f1[E2];
+                auto load2 = [&](int tb, int (&c)[E2], T (&f)[E2]) {
 #pragma unroll
-                    for (int q = 0; q < EJ2; q++) {
+                    for (int q = 0; q < E2; q++) {
                         const int t = tb + 32 * q + lane;
                         c[q] = -1;
                         f[q] = T(0);
@@ -967,13 +969,13 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
                     }
                 };
                 load2(t0, c1, f1);
-                for (; t0 < ee[r]; t0 += 32 * EJ2) {
-                    int c2[EJ2];
-                    T f2[EJ2], w2[EJ2];
-                    if (t0 + 32 * EJ2 < ee[r]) load2(t0 + 32 * EJ2, c2, f2);
+                for (; t0 < ee[r]; t0 += 32 * E2) {
+                    int c2[E2];
+                    T f2[E2], w2[E2];
+                    if (t0 + 32 * E2 < ee[r]) load2(t0 + 32 * E2, c2, f2);
                     unsigned nd = 0;
 #pragma unroll
-                    for (int q = 0; q < EJ2; q++) {
+                    for (int q = 0; q < E2; q++) {
                         const int c = c1[q];
                         w2[q] = T(0);
                         if (c >= 0) {
@@ -988,7 +990,7 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
                     }
                     if (__any_sync(FULL, nd != 0)) {
 #pragma unroll
-                        for (int q = 0; q < EJ2; q++) {
+                        for (int q = 0; q < E2; q++) {
                             const bool nq = (nd >> q) & 1u;
                             const T w = warp_wait_load(rc, yout + (nq ? c1[q] : 0), nq, lane);
                             if (nq) w2[q] = w;
@@ -996,10 +998,10 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
                     }
                     const int tq = ee[r] - t0;
 #pragma unroll
-                    for (int q = 0; q < EJ2; q++)
+                    for (int q = 0; q < E2; q++)
                         if (32 * q < tq) acc[r] = fma(f1[q], w2[q], acc[r]);
 #pragma unroll
-                    for (int q = 0; q < EJ2; q++) {
+                    for (int q = 0; q < E2; q++) {
                         c1[q] = c2[q];
                         f1[q] = f2[q];
                     }
