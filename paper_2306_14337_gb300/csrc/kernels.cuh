@@ -68,6 +68,15 @@ struct TaskCfg {
     // Claim-order entries p < 0 are packs of single-row tasks: pack -1 - p
     // holds the rows pack_rows[32 (-1 - p) + lane] (-1: empty lane).
     const int *pack_rows;
+    // Outside parts of CTA-task rows (optional, ext != null): claim-order
+    // entries e >= ext_base are warp items that sum row ext_rows[e - ext_base]
+    // over its dependencies outside its task and publish the sum in ext[row];
+    // cs_ext[row] splits the row's dependency slots (forward: outside
+    // [row start, cs_ext), backward: outside [cs_ext, row end)).
+    int ext_base;
+    const int *ext_rows;
+    const int *cs_ext;
+    void *ext;
 };
 
 struct RunCfg {

@@ -755,7 +755,7 @@ constexpr int EJ2 = 8;            // slots per lane of the further chunks of a l
 // (T), and per row up to zcap: the right-hand side term, the pivot scale (T)
 // and four slot bounds (int)
 __host__ __device__ constexpr size_t chain_smem_bytes(int zcap, size_t tsz) {
-    return ((size_t)5 * CB * TS + 6 * CB + 3 * (size_t)zcap) * tsz + 4 * sizeof(int) * (size_t)zcap;
+    return ((size_t)5 * CB * TS + 6 * CB + 3 * (size_t)zcap) * tsz + 5 * sizeof(int) * (size_t)zcap;
 }
 
 template <typename T, bool BACKWARD, bool TRANS>
@@ -780,6 +780,8 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
     T *mb = zs + zcap;                          // [zcap]: right-hand side term by step
     T *ms = mb + zcap;                          // [zcap]: pivot scale (1 without division)
     int4 *mi = reinterpret_cast<int4 *>(ms + zcap);   // [zcap]: slot bounds (see meta)
+    int *mo = reinterpret_cast<int *>(mi + zcap);      // [zcap]: 1 if the row's outside sum is an item's
+    T *ext = reinterpret_cast<T *>(tk.ext);
     auto row_of = [&](int k) { return BACKWARD ? hi - k : lo + k; };
     auto step_of = [&](int c) { return BACKWARD ? hi - c : c - lo; };
     // Slot bounds of the row at step k: x = first slot of the dependency
@@ -787,11 +789,19 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
     // [x, y), late [y, z), diag [z, w); backward: diag [x, z), late [z, y),
     // early [y, w)), its right-hand side term and pivot scale; cached in
     // shared memory by the prologue below for steps < zcap.
-    auto meta_g = [&](int k, int4 &q, T &base, T &scl) {
+    // With outside items (ext), the early range covers only the sources
+    // inside this task and `out` tells whether an item publishes the rest.
+    auto meta_g = [&](int k, int4 &q, T &base, T &scl, int &outside) {
         const int i = row_of(k);
         const int dg = P.diag[i];
         q.x = BACKWARD ? dg + 1 : P.lu_rp[i];
         q.w = BACKWARD ? P.lu_rp[i + 1] : dg;
+        outside = 0;
+        if (ext) {
+            const int ce = tk.cs_ext[i];
+            if (BACKWARD) { outside = ce < q.w; q.w = ce; }
+            else { outside = ce > q.x; q.x = ce; }
+        }
         q.y = tk.cs_late[i];
         q.z = tk.cs_diag[i];
         if (BACKWARD) base = yin[i];
@@ -804,8 +814,17 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
             base = mb[k];
             scl = ms[k];
         } else {
-            meta_g(k, q, base, scl);
+            int o_;
+            meta_g(k, q, base, scl, o_);
         }
+    };
+    auto outside_of = [&](int k) -> int {
+        if (k < zcap) return mo[k];
+        int4 q;
+        T b_, s_;
+        int o_;
+        meta_g(k, q, b_, s_, o_);
+        return o_;
     };
     {
         const int mm = min(m, zcap);
@@ -813,10 +832,11 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
         for (int k0 = threadIdx.x; k0 < mm; k0 += U * blockDim.x) {
             int4 q[U];
             T bs[U], sc[U];
+            int ou[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int k = k0 + u * blockDim.x;
-                if (k < mm) meta_g(k, q[u], bs[u], sc[u]);
+                if (k < mm) meta_g(k, q[u], bs[u], sc[u], ou[u]);
             }
 #pragma unroll
             for (int u = 0; u < U; u++) {
@@ -825,6 +845,7 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
                     mi[k] = q[u];
                     mb[k] = bs[u];
                     ms[k] = sc[u];
+                    mo[k] = ou[u];
                 }
             }
         }
@@ -1024,12 +1045,22 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
             sub[h * CB + lane] = s8;
         }
         named_barrier(1, nh * 32);
-        if (h == 0 && lane < cnt) {
+        if (h == 0) {
+            const bool own = lane < cnt;
             int4 mt;
-            T base, scl;
-            meta(k0 + lane, mt, base, scl);
-            const T e = (sub[lane] + sub[CB + lane]) + (sub[2 * CB + lane] + sub[3 * CB + lane]);
-            xbb[lane] = FOLD ? (base - e) * scl : base - e;
+            T base = T(0), scl = T(1);
+            int outside = 0;
+            if (own) {
+                meta(k0 + lane, mt, base, scl);
+                outside = ext ? outside_of(k0 + lane) : 0;
+            }
+            // the outside sum published by its item (polled; all lanes take part)
+            const T xo = warp_wait_load(rc, ext + (outside ? row_of(k0 + lane) : 0), outside != 0, lane);
+            if (own) {
+                T e = (sub[lane] + sub[CB + lane]) + (sub[2 * CB + lane] + sub[3 * CB + lane]);
+                if (outside) e += xo;
+                xbb[lane] = FOLD ? (base - e) * scl : base - e;
+            }
         }
     };
 
@@ -1135,6 +1166,67 @@ __device__ __forceinline__ void trisolve_pack(const DevPattern &P, const RunCfg 
     }
 }
 
+// The outside part of one row of a CTA task: the sum over its dependencies
+// in other tasks (a warp per row, loads first, next chunk in flight), published
+// for the row's CTA.  Runs on warps anywhere on the GPU, so the long paths'
+// CTAs only stream their own entries.
+template <typename T, bool BACKWARD>
+__device__ __forceinline__ void trisolve_ext(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
+                                             const T *__restrict__ F, T *yout, int i, int lane) {
+    constexpr int Q = 8;
+    const int tb = BACKWARD ? tk.cs_ext[i] : P.lu_rp[i];
+    const int te = BACKWARD ? P.lu_rp[i + 1] : tk.cs_ext[i];
+    auto load = [&](int t0, int (&c)[Q], T (&f)[Q]) {
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            const int t = t0 + 32 * q + lane;
+            c[q] = -1;
+            f[q] = T(0);
+            if (t < te) {
+                c[q] = P.lu_ci[t];
+                f[q] = F[t];
+            }
+        }
+    };
+    T acc = T(0);
+    int c1[Q];
+    T f1[Q];
+    load(tb, c1, f1);
+    for (int t0 = tb; t0 < te; t0 += 32 * Q) {
+        int c2[Q];
+        T f2[Q], v[Q];
+        if (t0 + 32 * Q < te) load(t0 + 32 * Q, c2, f2);
+        unsigned need = 0;
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            v[q] = T(0);
+            if (c1[q] >= 0) {
+                v[q] = ld_relaxed_v(yout + c1[q]);
+                if (is_marker(v[q])) need |= 1u << q;
+            }
+        }
+        if (__any_sync(FULL, need != 0)) {
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                const bool nq = (need >> q) & 1u;
+                const T w = warp_wait_load(rc, yout + (nq ? c1[q] : 0), nq, lane);
+                if (nq) v[q] = w;
+            }
+        }
+        const int tq = te - t0;
+#pragma unroll
+        for (int q = 0; q < Q; q++)
+            if (32 * q < tq) acc = fma(f1[q], v[q], acc);
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            c1[q] = c2[q];
+            f1[q] = f2[q];
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) publish(rc, reinterpret_cast<T *>(tk.ext) + i, acc);
+}
+
 // Packs, once per refactorization, the tiles the CTA tasks of the four solve
 // phases read: for every block b of every CTA task, the diag tile (rows of
 // block b, sources in block b) and the late tile (rows of block b + 1, sources
@@ -1212,6 +1304,8 @@ k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T
         if (tid < 0)
             trisolve_pack<T, BACKWARD, TRANS>(P, rc, tk, F, rcp, rhs, sp, yin, yout, out, accumulate, -1 - tid,
                                               lane);
+        else if (tid >= tk.ext_base)
+            trisolve_ext<T, BACKWARD>(P, rc, tk, F, yout, tk.ext_rows[tid - tk.ext_base], lane);
         else
             trisolve_task<T, BACKWARD, TRANS>(P, rc, tk, F, rcp, rhs, sp, yin, yout, out, accumulate, tid, loc,
                                               lane);
@@ -1682,6 +1776,9 @@ struct kkt_ctx {
     void *d_tiles = nullptr;         // packed tiles, 4 phases x nblk x 2 x 32 x 32
     bool tiles_fresh = false;        // d_tiles match the current factors
     std::vector<int> chain_h;        // CTA tasks of the single-system solves (host copy)
+    // outside items of CTA-task rows: splits and rows per direction, order lengths
+    const int *ce_fwd = nullptr, *ce_bwd = nullptr, *xr_fwd = nullptr, *xr_bwd = nullptr;
+    int nord_f = 0, nord_b = 0;
     size_t solve_smem = 0, bsolve_smem = 0;
     unsigned long long *h_norms = nullptr;  // pinned
     int grid = 0, solve_grid = 0, bsolve_grid = 0, cta_warps = WARPS, solve_warps = SWARPS, cap = 0;
@@ -1819,7 +1916,7 @@ static kkt_status upload(kkt_ctx *c) {
     CK(cudaMalloc(&c->d_s, n * sizeof(double)));
     CK(cudaMalloc(&c->d_sp, n * sizeof(double)));
     CK(cudaMalloc(&c->d_rho, n * sizeof(double)));
-    CK(cudaMalloc(&c->d_y, 2 * (size_t)n * sizeof(double)));
+    CK(cudaMalloc(&c->d_y, 4 * (size_t)n * sizeof(double)));   // y, z, outside sums (forward, backward)
     CK(cudaMalloc(&c->d_status, ST_WORDS * sizeof(int)));
     CK(cudaMalloc(&c->d_norms, NM_WORDS * sizeof(unsigned long long)));
     CK(cudaMalloc(&c->d_sched, sizeof(Sched)));
@@ -1967,7 +2064,52 @@ static kkt_status upload(kkt_ctx *c) {
             of1.swap(f2);
             ob1.swap(b2);
         }
-        // blocks of the CTA tasks (for the packed tiles)
+        // Outside items: every row of a CTA task with dependencies in other
+        // tasks gets a warp item for that part, claimed with the tasks:
+        // forward by the row's depth among the depth-ordered tasks (its outside
+        // sources are deeper), backward right after its task's position (its
+        // outside sources are ancestors in earlier tasks).
+        std::vector<int> ce_f(n, 0), ce_b(n, 0), xr_f, xr_b;
+        {
+            std::vector<int> task_of_row(n, -1);
+            for (int T : chain)
+                for (int i = a.task_lo[T]; i <= a.task_hi[T]; i++) task_of_row[i] = T;
+            const int *ci = a.lu_ci.data();
+            for (int T : chain) {
+                const int lo = a.task_lo[T], hi = a.task_hi[T];
+                for (int i = lo; i <= hi; i++) {
+                    const int rb = a.lu_rp[i], dg = a.diag[i], re = a.lu_rp[i + 1];
+                    ce_f[i] = (int)(std::lower_bound(ci + rb, ci + dg, lo) - ci);
+                    ce_b[i] = (int)(std::upper_bound(ci + dg + 1, ci + re, hi) - ci);
+                    if (ce_f[i] > rb) xr_f.push_back(i);
+                    if (ce_b[i] < re) xr_b.push_back(i);
+                }
+            }
+            // forward: merge into the depth-ordered part after the prefix and packs
+            const size_t head = (size_t)nlong1 + (pack_rows.size() / 32);
+            std::vector<std::pair<int, int>> tail;        // (depth key, entry)
+            for (size_t q = head; q < of1.size(); q++) tail.push_back({depth[of1[q]], of1[q]});
+            for (size_t k = 0; k < xr_f.size(); k++) tail.push_back({a.level_u[xr_f[k]], nt + (int)k});
+            std::stable_sort(tail.begin(), tail.end(), [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+                return x.first > y.first;
+            });
+            of1.resize(head);
+            for (auto &e : tail) of1.push_back(e.second);
+            // backward: by the height of the row's task's top, after the tasks
+            // of that height (packs keep their place at the end)
+            std::vector<std::array<int, 3>> bk;           // (height key, tie, entry)
+            for (size_t q = 0; q < ob1.size(); q++) {
+                const int e = ob1[q];
+                bk.push_back({e >= 0 ? top[e] : -1, 0, e});
+            }
+            for (size_t k = 0; k < xr_b.size(); k++) bk.push_back({top[task_of_row[xr_b[k]]], 1, nt + (int)k});
+            std::stable_sort(bk.begin(), bk.end(), [](const std::array<int, 3> &x, const std::array<int, 3> &y) {
+                if (x[0] != y[0]) return x[0] > y[0];
+                return x[1] < y[1];
+            });
+            ob1.clear();
+            for (auto &e : bk) ob1.push_back(e[2]);
+        }
         std::vector<int> blk0(chain.size() + 1, 0), binfo;
         for (size_t q = 0; q < chain.size(); q++) {
             const int T = chain[q], nbq = (len[T] + CB - 1) / CB;
@@ -2009,8 +2151,9 @@ static kkt_status upload(kkt_ctx *c) {
             }
         }
         int *d = nullptr;
-        const size_t words = 3 * (size_t)nt + 3 * (size_t)nt + chain.size() + 4 * (size_t)n + blk0.size() +
-                             binfo.size() + pack_rows.size();
+        const size_t words = 3 * (size_t)nt + 3 * (size_t)(nt + xr_f.size() + xr_b.size()) + chain.size() +
+                             4 * (size_t)n + blk0.size() + binfo.size() + pack_rows.size() + 2 * (size_t)n +
+                             xr_f.size() + xr_b.size();
         CK(cudaMalloc(&d, words * sizeof(int)));
         size_t o = 0;
         auto put = [&](const std::vector<int> &v) -> const int * {
@@ -2029,7 +2172,7 @@ static kkt_status upload(kkt_ctx *c) {
         c->tk.order_topo = put(ot);
         c->tk1.task_lo = c->tk.task_lo;
         c->tk1.task_hi = c->tk.task_hi;
-        c->tk1.ntasks = (int)of1.size();
+        c->tk1.ntasks = (int)of1.size();     // per phase in tasks_of
         c->tk1.order_f = put(of1);
         c->tk1.order_b = put(ob1);
         c->tk1.order_topo = put(ot1);
@@ -2038,6 +2181,13 @@ static kkt_status upload(kkt_ctx *c) {
         c->chain_h = chain;
         c->tk1.chain_blk0 = put(blk0);
         c->tk1.pack_rows = put(pack_rows);
+        c->ce_fwd = put(ce_f);
+        c->ce_bwd = put(ce_b);
+        c->xr_fwd = put(xr_f);
+        c->xr_bwd = put(xr_b);
+        c->nord_f = (int)of1.size();
+        c->nord_b = (int)ob1.size();
+        c->tk1.ext_base = nt;
         c->blk_info = put(binfo);
         c->nblk = blk0.back();
         c->cs_fwd = put(std::vector<int>(csl.begin(), csl.begin() + n));
@@ -2288,6 +2438,14 @@ static TaskCfg tasks_of(const kkt_ctx *c, bool backward, bool trans) {
     TaskCfg t = c->tk1;
     t.cs_late = backward ? c->cs_bwd : c->cs_fwd;
     t.cs_diag = backward ? c->csd_bwd : c->csd_fwd;
+    t.ntasks = backward ? c->nord_b : c->nord_f;
+    t.cs_ext = backward ? c->ce_bwd : c->ce_fwd;
+    t.ext_rows = backward ? c->xr_bwd : c->xr_fwd;
+    {   // outside sums after y and z in the work vector (4n doubles)
+        const size_t tsz_ = c->opt.factor_fp32 ? sizeof(float) : sizeof(double);
+        const size_t n = (size_t)c->an.n;
+        t.ext = (char *)c->d_y + (2 + (backward ? 1 : 0)) * n * tsz_;
+    }
     const int ph = (trans ? 2 : 0) + (backward ? 1 : 0);
     const size_t tsz = c->opt.factor_fp32 ? sizeof(float) : sizeof(double);
     t.tiles = c->d_tiles ? (const void *)((const char *)c->d_tiles + (size_t)ph * c->nblk * 2 * CB * CB * tsz)
@@ -2300,7 +2458,7 @@ static kkt_status launch_solve(kkt_ctx *c, const double *b, double *x, int accum
     const int n = c->an.n;
     T *y = (T *)c->d_y, *z = y + n;
     const T *L = (const T *)c->d_lu, *R = (const T *)c->d_rcp;
-    CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
+    CK(cudaMemsetAsync(y, 0xff, 4 * (size_t)n * sizeof(T), s));   // y, z and the outside sums
     k_trisolve<T, false, false><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
         c->P, c->rc, tasks_of(c, false, false), L, R, b, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
@@ -2318,7 +2476,7 @@ static kkt_status launch_solve_t(kkt_ctx *c, const double *g, double *lam, int a
     const int n = c->an.n;
     T *y = (T *)c->d_y, *z = y + n;
     const T *L = (const T *)c->d_lut, *R = (const T *)c->d_rcp;
-    CK(cudaMemsetAsync(y, 0xff, 2 * (size_t)n * sizeof(T), s));
+    CK(cudaMemsetAsync(y, 0xff, 4 * (size_t)n * sizeof(T), s));   // y, z and the outside sums
     k_trisolve<T, false, true><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
         c->P, c->rc, tasks_of(c, false, true), L, R, g, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
@@ -2959,7 +3117,10 @@ kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
         s.rho = c->d_rho;
         s.tau_rel = c->tau_rel;
         s.n = c->an.n;
-        for (int ph = 0; ph < 4; ph++) s.tkc[ph] = tasks_of(c, ph & 1, ph >= 2);
+        for (int ph = 0; ph < 4; ph++) {
+            s.tkc[ph] = tasks_of(c, ph & 1, ph >= 2);
+            s.tkc[ph].ext = nullptr;           // a queue's CTA tasks sum their outside parts themselves
+        }
     }
     q->rc = ctxs[0]->rc;
     q->rc.status = q->d_status;
