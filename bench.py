@@ -212,7 +212,9 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": us, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": us / 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "n": seq.n, "nnz": seq.nnz},
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n": seq.n, "nnz": seq.nnz, "value_sets": seq.steps,
+                   "l2": "host cores (no GPU cache)", "parallelism": "one host core"},
         "cpu_baseline": {"value": us, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{done} whole steps (refactor, solve, refine, transposed solve, adjoint) "
                                    f"of the {args.workload} sequence, single-threaded"},
