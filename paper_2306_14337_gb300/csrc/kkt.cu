@@ -492,12 +492,13 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                 w[dp] = (T)pv;
             }
             __syncwarp();
-            // U part first (the signals of the rows below), then the reciprocal pivot
-            for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + (rb + t), w[t]);
+            // the reciprocal pivot first (the rows below wait on it, then reload
+            // the U part, which is on its way by then), then the U part
             if (lane == 0) {
                 LU[rb + dp] = w[dp];
                 if (i != rc.unpublished_row) publish(rc, rcp + i, T(1) / w[dp]);
             }
+            for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + (rb + t), w[t]);
             for (int t = lane; t < len; t += 32) {
                 if (t < dp) LU[rb + t] = w[t];
                 LUT[P.tpos[rb + t]] = w[t];
@@ -730,9 +731,11 @@ __device__ __forceinline__ void trisolve_task(const DevPattern &P, const RunCfg 
 //
 // Warp 0 (the walker) solves block b row after row: lane j owns row j of the
 // block, the result of lane s is broadcast and every lane applies the diag
-// entry of its row to it (and the late entry of its row in block b + 1, so the
-// late part of the next block is complete when this block is).  The other
-// warps (the helpers) meanwhile gather block b + 1: the right-hand side minus
+// entry of its row to it.  Warp 1 (on another FP64 pipe) applies each result
+// as it appears in shared memory to the late entries of block b + 1's rows, so
+// the late part of the next block is complete when this block is and a walker
+// step is one shuffle and one dependent multiply-add.  The other warps (the
+// helpers) meanwhile gather block b + 1: the right-hand side minus
 // the early part (a warp per row, external sources polled in global memory)
 // and the two 32 x 32 tiles of diag / late entries the walker reads next.
 // Where the phase divides by the pivot, the helpers fold the reciprocal pivot
@@ -755,7 +758,7 @@ constexpr int EJ2 = 8;            // slots per lane of the further chunks of a l
 // (T), and per row up to zcap: the right-hand side term, the pivot scale (T)
 // and four slot bounds (int)
 __host__ __device__ constexpr size_t chain_smem_bytes(int zcap, size_t tsz) {
-    return ((size_t)5 * CB * TS + 6 * CB + 3 * (size_t)zcap) * tsz + 5 * sizeof(int) * (size_t)zcap;
+    return ((size_t)5 * CB * TS + 8 * CB + 3 * (size_t)zcap) * tsz + 5 * sizeof(int) * (size_t)zcap;
 }
 
 template <typename T, bool BACKWARD, bool TRANS>
@@ -774,7 +777,9 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
     T *xb = tl + 2 * CB * TS;                  // [2][CB]: right-hand side minus the early part
     T *red = xb + 2 * CB;                      // [CB][TS]: per-lane partial early sums
     T *sub = red + CB * TS;                    // [4][CB]: partial sums of 8 lanes each
-    T *zs = sub + 4 * CB;                      // [zcap]: results of this task by step
+    T *zbuf = sub + 4 * CB;                    // [CB]: the walker's results of the block, marker until written
+    T *lateb = zbuf + CB;                      // [CB]: minus the late part of the next block's rows
+    T *zs = lateb + CB;                        // [zcap]: results of this task by step
     const int zcap = tk.zcap;
     const T *tiles = reinterpret_cast<const T *>(tk.tiles) + (size_t)tk.chain_blk0[cidx] * 2 * CB * CB;
     T *mb = zs + zcap;                          // [zcap]: right-hand side term by step
@@ -854,8 +859,8 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
 
     // helpers: prepare block B (x - early, diag tile) and the late tile of block B + 1
     auto prepare = [&](int B) {
-        if (wid == 0 || B >= nb) return;
-        const int nh = nw - 1, h = wid - 1;
+        if (wid < 2 || B >= nb) return;
+        const int nh = nw - 2, h = wid - 2;
         T *tdb = td + (B & 1) * CB * TS, *tlb = tl + (B & 1) * CB * TS, *xbb = xb + (B & 1) * CB;
         const int k0 = B * CB, cnt = min(CB, m - k0);
         const int cnt1 = (B + 1 < nb) ? min(CB, m - k0 - CB) : 0;
@@ -1064,23 +1069,29 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
         }
     };
 
+    T marker;
+    {
+        const unsigned long long ones = ~0ull;
+        memcpy(&marker, &ones, sizeof(T));
+    }
+    if (threadIdx.x < CB) {
+        zbuf[threadIdx.x] = marker;
+        lateb[threadIdx.x] = T(0);
+    }
     prepare(0);
     __syncthreads();
-    T late = T(0);                              // walker: minus the late part of the next block's row
     for (int b = 0; b < nb; b++) {
+        const int k0 = b * CB, cnt = min(CB, m - k0);
         if (wid == 0) {
             const T *tdb = td + (b & 1) * CB * TS + lane * TS;
-            const T *tlb = tl + (b & 1) * CB * TS + lane * TS;
-            const int k0 = b * CB, cnt = min(CB, m - k0);
             const bool own = lane < cnt;
-            T acc = own ? xb[(b & 1) * CB + lane] + late : T(0);
+            T acc = own ? xb[(b & 1) * CB + lane] + lateb[lane] : T(0);
             T orc = T(1);
             if (DIV && !FOLD && own) {
                 int4 mt;
                 T bs_;
                 meta(k0 + lane, mt, bs_, orc);
             }
-            late = T(0);
             T z = T(0);
 #pragma unroll
             for (int s = 0; s < CB; s++) {
@@ -1088,8 +1099,8 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
                     const T zl = (DIV && !FOLD) ? acc * orc : acc;
                     const T zb = __shfl_sync(FULL, zl, s);
                     if (lane == s) z = zl;
+                    if (lane == 0) *(volatile T *)(zbuf + s) = is_marker(zb) ? T(NAN) : zb;
                     acc = fma(-tdb[s], zb, acc);
-                    late = fma(-tlb[s], zb, late);
                 }
             }
             if (own) {
@@ -1107,6 +1118,27 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
                     out[oo] = accumulate ? out[oo] + w : w;
                 }
             }
+        } else if (wid == 1) {
+            // late part of block b + 1's rows, from the walker's results as they appear
+            const T *tlb = tl + (b & 1) * CB * TS + lane * TS;
+            T late = T(0);
+            bool ok = true;
+            for (int s = 0; s < cnt; s++) {
+                T zb = *(volatile T *)(zbuf + s);
+                long long it = 0;
+                while (ok && is_marker(zb)) {           // the walker never waits: a short spin
+                    if (++it > rc.spin_limit) {
+                        atomicExch(rc.status + ST_TIMEOUT, 1);
+                        atomicExch(rc.status + ST_ABORT, 1);
+                        ok = false;
+                    }
+                    zb = *(volatile T *)(zbuf + s);
+                }
+                late = fma(-tlb[s], ok ? zb : T(0), late);
+            }
+            __syncwarp();
+            lateb[lane] = late;
+            zbuf[lane] = marker;                        // for the next block (after the barrier)
         } else {
             prepare(b + 1);
         }
