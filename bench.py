@@ -396,6 +396,12 @@ def run_native(args, ws, rank, local):
                          "transpose": statistics.mean(i[1] for i in iters)},
         "omega_max": max(omegas), "status": int(st_code), "perturbed_pivots": npert,
         "roofline": roof,
+        # Why the fraction is low: the refactorization is a chain of dependent
+        # rows, one hand-off per level of the elimination DAG.
+        "critical_path": {"refactor_levels": st["n_levels"],
+                          "refactor_us_per_level": ph_ms["refactor"] * 1e3 / st["n_levels"],
+                          "solve_levels": {"forward": st["n_levels"], "backward": st["n_levels_u"]},
+                          "solve_tasks": st["n_tasks"], "longest_task_rows": st["max_task"]},
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_us_per_system(e2e_s, args.steps, ws), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (nnz + 2 * n), "d2h_bytes_per_step": 8 * (nnz + 2 * n)},

@@ -13,6 +13,12 @@
 // The claim queue resets itself: the last warp to find it empty zeroes it for
 // the next launch, so launches need no host-side preparation and can be
 // replayed from a CUDA graph.
+//
+// Kinds of work in a solve phase (see TaskCfg): the longest tasks each run on
+// a whole CTA (one walker warp, one warp for late updates, helper warps over
+// packed 32 x 32 tiles); short tasks run on one warp; single-row tasks run 32
+// to a warp as packs; and the parts of a CTA task's rows that depend on other
+// tasks are summed ahead of time by warp items, so the walker only adds them.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>

@@ -43,21 +43,11 @@ constexpr int WARPS = 8;  // warps per CTA of the persistent kernels
 // ---------------------------------------------------------------------------
 // synchronisation helpers
 
-__device__ __forceinline__ int ld_acquire(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ int ld_relaxed(const int *p) {
     int v;
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(int *p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-template <typename T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -1472,61 +1462,6 @@ __global__ void k_vscale(double *__restrict__ v, const double *__restrict__ w, d
 // task of one system, the row's columns across the lanes) through Strided
 // accessors.  The B systems' independent dependency chains run side by side,
 // so the batch fills the GPU that one latency-bound system leaves idle.
-
-__device__ __forceinline__ double ld_acquire_v(const double *p) {
-    double v;
-    asm volatile("ld.acquire.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ float ld_acquire_v(const float *p) {
-    float v;
-    asm volatile("ld.acquire.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_v(double *p, double v) {
-    asm volatile("st.release.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
-}
-__device__ __forceinline__ void st_release_v(float *p, float v) {
-    asm volatile("st.release.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
-
-// Like warp_wait_load, with acquire semantics on the value each lane finally
-// reads (the producer releases it after writing the data it guards).
-template <typename T>
-__device__ __forceinline__ T warp_wait_acquire(const RunCfg &rc, const T *p, bool need, int lane) {
-    T v = need ? ld_acquire_v(p) : T(0);
-    unsigned pend = __ballot_sync(FULL, need && is_marker(v));
-    while (pend) {
-        const int leader = __ffs(pend) - 1;
-        int bad = 0;
-        if (lane == leader) {
-            unsigned ns = 32;
-            long long it = 0;
-            for (;;) {
-                __nanosleep(ns);
-                v = ld_relaxed_v(p);
-                if (!is_marker(v)) break;
-                if (ns < rc.poll_ns_max) ns <<= 1;
-                if ((++it & 7) == 0) {
-                    if (ld_relaxed(rc.status + ST_ABORT)) { bad = 1; break; }
-                    if (it > rc.spin_limit) {
-                        atomicExch(rc.status + ST_TIMEOUT, 1);
-                        atomicExch(rc.status + ST_ABORT, 1);
-                        bad = 1;
-                        break;
-                    }
-                }
-            }
-        }
-        if (__shfl_sync(FULL, bad, leader)) {
-            if (is_marker(v)) v = T(0);
-            break;
-        }
-        if ((pend >> lane) & 1u) v = ld_acquire_v(p);
-        pend = __ballot_sync(FULL, ((pend >> lane) & 1u) && is_marker(v));
-    }
-    return v;
-}
 
 // per-(row, system) scaling, ||A||_inf per system
 __global__ void k_bscale(DevPattern P, int B, const double *__restrict__ aval, double *__restrict__ s_orig,
