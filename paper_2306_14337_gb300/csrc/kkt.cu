@@ -30,6 +30,8 @@
 #include <string>
 #include <vector>
 #include <set>
+#include <map>
+#include <mutex>
 
 #include "kkt.h"
 #include "analysis.h"
@@ -390,10 +392,31 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                     prefetch(t + 1, __shfl_sync(FULL, md, k1), __shfl_sync(FULL, mub, k1),
                              __shfl_sync(FULL, mue, k1), __shfl_sync(FULL, mmo, k1));
                 }
-                // this step: reciprocal pivot and first block, polled only if unpublished
+                // this step: reciprocal pivot and first block.  If the prefetch
+                // came too early, the reciprocal is reloaded together with the
+                // missing values (one round trip) and polled only if still
+                // unpublished; the next step's prefetch, just as stale, is then
+                // sent again.
                 if (__any_sync(FULL, lane == 0 && is_marker(r))) {
-                    const T w0 = warp_wait_load(rc, rcp + d, lane == 0, lane);
-                    if (lane == 0) r = w0;
+                    if (lane == 0) r = ld_relaxed_v(rcp + d);
+    #pragma unroll
+                    for (int q = 0; q < UJ; q++)
+                        if (lo[q] >= 0 && is_marker(uv[q])) uv[q] = ld_relaxed_v(LU + (ub + 1 + 32 * q + lane));
+                    if (__any_sync(FULL, lane == 0 && is_marker(r))) {
+                        const T w0 = warp_wait_load(rc, rcp + d, lane == 0, lane);
+                        if (lane == 0) r = w0;
+                    }
+                    if (t + 1 < dp && __any_sync(FULL, lane == 0 && is_marker(pr))) {
+                        const int k1 = (t + 1) & 31;
+                        const int d1 = __shfl_sync(FULL, md, k1), ub1 = __shfl_sync(FULL, mub, k1),
+                                  ue1 = __shfl_sync(FULL, mue, k1);
+                        pr = ld_relaxed_v(rcp + d1);
+    #pragma unroll
+                        for (int q = 0; q < UJ; q++) {
+                            const int u = ub1 + 1 + 32 * q + lane;
+                            if (u < ue1) pu[q] = ld_relaxed_v(LU + u);
+                        }
+                    }
                 }
                 const T l = w[t] * __shfl_sync(FULL, r, 0);
                 unsigned need = 0;
@@ -419,9 +442,15 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                 }
                 // rounds past the end of the pivot row are skipped as a whole
                 // (an FP64 instruction costs the same with idle lanes)
+                // the round's targets are distinct: all loads, then all updates
+                {
+                    T x[UJ];
     #pragma unroll
-                for (int q = 0; q < UJ; q++)
-                    if (32 * q < ue - ub - 1 && lo[q] >= 0) w[lo[q]] -= l * uv[q];
+                    for (int q = 0; q < UJ; q++) x[q] = (32 * q < ue - ub - 1 && lo[q] >= 0) ? w[lo[q]] : T(0);
+    #pragma unroll
+                    for (int q = 0; q < UJ; q++)
+                        if (32 * q < ue - ub - 1 && lo[q] >= 0) w[lo[q]] = x[q] - l * uv[q];
+                }
                 // remaining blocks of long pivot rows, double-buffered: the next
                 // block's targets and values are in flight while this one updates
                 auto load_blk = [&](int u0, int (&bl)[UJ], T (&bv)[UJ]) {
@@ -456,9 +485,12 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                                 if (nq) cv[q] = v;
                             }
                         }
+                        T x[UJ];
+    #pragma unroll
+                        for (int q = 0; q < UJ; q++) x[q] = (u0 + 32 * q < ue && cl[q] >= 0) ? w[cl[q]] : T(0);
     #pragma unroll
                         for (int q = 0; q < UJ; q++)
-                            if (u0 + 32 * q < ue && cl[q] >= 0) w[cl[q]] -= l * cv[q];
+                            if (u0 + 32 * q < ue && cl[q] >= 0) w[cl[q]] = x[q] - l * cv[q];
     #pragma unroll
                         for (int q = 0; q < UJ; q++) {
                             cl[q] = nl[q];
@@ -1787,6 +1819,24 @@ struct DeviceGuard {
 };
 
 inline int blocks_for(long long threads, int bs) { return (int)((threads + bs - 1) / bs); }
+
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The limit belongs to the kernel, not to a context, so it is
+// only ever raised: a context created later with smaller needs must not break
+// the launches of one created earlier.
+cudaError_t ensure_smem(const void *f, size_t bytes) {
+    static std::mutex m;
+    static std::map<std::pair<const void *, int>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(m);
+    size_t &have = done[{f, dev}];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
 }  // namespace
 
 // The entry points below have C linkage through their declarations in kkt.h.
@@ -1905,10 +1955,10 @@ static kkt_status upload(kkt_ctx *c) {
     c->smem = (size_t)nw * cap * (tsz + sizeof(int));
     int per_sm = 0;
     if (f32) {
-        CK(cudaFuncSetAttribute(k_refactor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+        CK(ensure_smem((const void *)k_refactor<float>, c->smem));
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refactor<float>, nw * 32, c->smem));
     } else {
-        CK(cudaFuncSetAttribute(k_refactor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+        CK(ensure_smem((const void *)k_refactor<double>, c->smem));
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refactor<double>, nw * 32, c->smem));
     }
     if (per_sm < 1) { g_last_error = "refactor kernel does not fit on an SM"; return KKT_ERR_CUDA; }
@@ -2185,7 +2235,7 @@ static kkt_status upload(kkt_ctx *c) {
         c->solve_smem = std::max((size_t)snw * c->tk1.cap * tsz,
                                  c->tk1.nchain ? chain_smem_bytes(c->tk1.zcap, tsz) : 0);
         auto setsm = [&](const void *f) {
-            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->solve_smem);
+            return ensure_smem(f, c->solve_smem);
         };
         int per_sm_s = 0;
         if (f32) {
@@ -2232,7 +2282,7 @@ static kkt_status upload(kkt_ctx *c) {
         c->device_bytes += (2 * nlu + 3 * (size_t)n) * Bc * tsz + 3 * (size_t)n * Bc * sizeof(double);
         c->bsolve_smem = (size_t)nw * c->tk.cap * tsz;
         auto setb = [&](const void *f, size_t bytes) {
-            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            return ensure_smem(f, bytes);
         };
         if (f32) {
             CK(setb((const void *)k_brefactor<float>, c->smem));
@@ -2931,11 +2981,11 @@ struct kkt_queue {
 };
 
 template <typename T> static kkt_status q_set_smem(kkt_queue *q) {
-    CK(cudaFuncSetAttribute(k_qrefactor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_ref));
-    CK(cudaFuncSetAttribute(k_qtrisolve<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_sol));
-    CK(cudaFuncSetAttribute(k_qtrisolve<T, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_sol));
-    CK(cudaFuncSetAttribute(k_qtrisolve<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_sol));
-    CK(cudaFuncSetAttribute(k_qtrisolve<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q->smem_sol));
+    CK(ensure_smem((const void *)k_qrefactor<T>, q->smem_ref));
+    CK(ensure_smem((const void *)k_qtrisolve<T, false, false>, q->smem_sol));
+    CK(ensure_smem((const void *)k_qtrisolve<T, true, false>, q->smem_sol));
+    CK(ensure_smem((const void *)k_qtrisolve<T, false, true>, q->smem_sol));
+    CK(ensure_smem((const void *)k_qtrisolve<T, true, true>, q->smem_sol));
     return KKT_OK;
 }
 

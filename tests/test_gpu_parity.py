@@ -86,6 +86,21 @@ def test_refactor_parity_2000bus(step):
     _check_factors(S, o)
 
 
+def test_contexts_of_different_sizes_coexist():
+    """A kernel's shared-memory limit is per kernel, not per context: creating
+    a context with smaller rows after a larger one must not break the larger
+    one's launches."""
+    big_s, small_s = _seq(1), _seq(0)
+    big = KKTSolver(big_s.n, big_s.indptr, big_s.indices)
+    small = KKTSolver(small_s.n, small_s.indptr, small_s.indices, cta_warps=2)
+    for S, s in ((big, big_s), (small, small_s), (big, big_s)):
+        b = _t(s.csr(1) @ s.x_true(1))
+        S.refactor(_t(s.values(1)))
+        x = S.solve(b)
+        info = S.refine(b, x, tol=1e-14, max_it=20)
+        assert info["converged"] and S.status()[0] == _capi.KKT_OK, info
+
+
 @pytest.mark.parametrize("cfg,steps", [(0, range(10)), (1, (0, 7, 15, 29))])
 def test_solve_refine_sequence(cfg, steps):
     """Refactor and solve a whole value sequence on one context (flags and
