@@ -376,10 +376,10 @@ def run_native(args, ws, rank, local):
                    "transpose": 1 + statistics.mean(i[1] for i in iters)}.get(dom, 1)
         by = st["bytes_solve"] * nsolves
         achieved = by / (ph_ms[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": f"{dom} (k_fsolve/k_bsolve)", "achieved": achieved,
+        roof = {"bound": "hbm", "kernel": f"{dom} (k_trisolve)", "achieved": achieved,
                 "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm,
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": by,
-                "traffic": committed_traffic("k_fsolve_f64", args.workload)}
+                "traffic": committed_traffic("k_trisolve_f64", args.workload)}
     ref_bytes = st["bytes_refactor"]
     line = {
         "metric": METRIC, "value": us, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -7,15 +7,22 @@
 //          at the start of every row of k_refactor;
 //   Sec. 5.2 Algorithm 1 (row-wise, dependency-driven LU)
 //       -> k_refactor: one warp per row of the combined L+U (CSR), rows
-//          claimed deepest first, ready flags on the rows it depends on,
-//          the row staged in shared memory, updates placed by a binary search
-//          of the row's sorted column list (no atomics);
+//          claimed deepest first, the published values themselves as ready
+//          signals, the row staged in shared memory, updates placed through
+//          precomputed update maps (or a binary search of the row's sorted
+//          columns), no atomics;
 //   Sec. 5.2 Algorithm 2 (dependency-driven triangular solve)
-//       -> k_fsolve / k_bsolve and the transposed pair k_tfsolve / k_tbsolve,
-//          one warp per row, permutation and scaling fused at entry and exit;
+//       -> k_trisolve<T, BACKWARD, TRANS>: the forward and backward solves
+//          and the transposed pair, over longest-path tasks of the
+//          elimination tree (long ones on a CTA each), permutation and
+//          scaling fused at entry and exit;
 //   Sec. 5.1 iterative refinement rho = r - K dx, K delta = rho, dx += delta
 //       -> k_resid (FP64 CSR residual fused with the infinity norms) and the
-//          refinement loop in kkt_refine (the update is fused into k_bsolve).
+//          refinement loop in kkt_refine (the update is fused into the
+//          backward solve); FGMRES with CGS2 through k_spmv, k_mdot, k_vcomb;
+//   same-pattern batches and uneven queues
+//       -> k_brefactor / k_btrisolve (batch innermost) and k_qrefactor /
+//          k_qtrisolve (several patterns in one launch, recorded in a graph).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -257,16 +264,6 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
-}
-
-// ---------------------------------------------------------------------------
-// helpers for latency hiding
-
-// Prefetch the cache lines of [p, p + bytes) into L1, one line per lane.
-__device__ __forceinline__ void prefetch_l1(const void *p, long long bytes, int lane) {
-    const char *a = (const char *)((uintptr_t)p & ~(uintptr_t)127);
-    const long long nl = ((const char *)p + bytes - a + 127) / 128;
-    for (long long k = lane; k < nl; k += 32) asm volatile("prefetch.global.L1 [%0];" ::"l"(a + k * 128));
 }
 
 // ---------------------------------------------------------------------------
