@@ -233,7 +233,7 @@ kkt_status kkt_export_factors(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
 
 /*
  * Device trace of the most recent launch of one phase (options.trace = 1):
- * phase 0 refactorization (work item = row in claim order), 1 forward solve,
+ * phase 0 refactorization (work item = row, numbered like kkt_export_symbolic), 1 forward solve,
  * 2 backward solve, 3 transposed forward, 4 transposed backward (work item =
  * task in claim order, followed by the long tasks that ran on a CTA each, in
  * decreasing length).  out_host receives 2 words per item, the %globaltimer

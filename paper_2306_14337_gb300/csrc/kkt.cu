@@ -538,9 +538,10 @@ k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const doubl
     for (;;) {
         const int slot = claim_row(rc, lane);
         if (slot >= P.n) break;
-        trace_mark(rc, 0, slot, 0, lane);
-        refactor_row<T>(P, rc, aval, sp, LU, LUT, rcp, tau, P.order_f[slot], sval, scol, gw, lane);
-        trace_mark(rc, 0, slot, 1, lane);
+        const int row = P.order_f[slot];
+        trace_mark(rc, 0, row, 0, lane);
+        refactor_row<T>(P, rc, aval, sp, LU, LUT, rcp, tau, row, sval, scol, gw, lane);
+        trace_mark(rc, 0, row, 1, lane);
     }
     if (lane == 0) finish_launch(rc, e);
 }
@@ -3476,8 +3477,21 @@ kkt_status kkt_export_trace(kkt_ctx *c, int phase, unsigned long long *out_host,
     const long long items = phase == TR_REFACTOR ? c->an.n : c->tk.ntasks;
     const long long m = std::min(items, max_items);
     CK(cudaDeviceSynchronize());
-    CK(cudaMemcpy(out_host, c->d_trace + phase * c->rc.trace_stride, 2 * m * sizeof(unsigned long long),
-                  cudaMemcpyDeviceToHost));
+    if (phase == TR_REFACTOR) {
+        // recorded by internal row; returned by row in the caller's numbering
+        std::vector<unsigned long long> h(2 * (size_t)items);
+        CK(cudaMemcpy(h.data(), c->d_trace, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        for (long long i = 0; i < items; i++) {
+            const long long v = c->an.view_of[i];
+            if (v < m) {
+                out_host[2 * v] = h[2 * i];
+                out_host[2 * v + 1] = h[2 * i + 1];
+            }
+        }
+    } else {
+        CK(cudaMemcpy(out_host, c->d_trace + phase * c->rc.trace_stride, 2 * m * sizeof(unsigned long long),
+                      cudaMemcpyDeviceToHost));
+    }
     if (n_items) *n_items = m;
     return KKT_OK;
 }

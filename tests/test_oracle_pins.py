@@ -444,3 +444,51 @@ def test_generator_shape_and_quasidefinite():
     assert np.all(np.diag(C) < 0) and np.count_nonzero(C - np.diag(np.diag(C))) == 0
     for cfg, n in ((1, 14000), (2, 70000)):
         assert config_sequence(cfg).n == n
+
+
+def test_oracle_scaled_residual_hand_computed_3x3():
+    """omega = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) on a 3x3
+    case worked by hand (the scaled residual of the refinement target, Sec. 5.3
+    tolerance 1e-14).
+
+        A = [[4, -1, 0], [-2, 5, 1], [0, 3, -6]], x = [1, -2, 1/2],
+        b = [7, -11, -8]
+        A x = [4 + 2, -2 - 10 + 1/2, -6 - 3] = [6, -23/2, -9]
+        rho = b - A x = [1, 1/2, 1]               -> ||rho||_inf = 1
+        row sums of |A|: 5, 8, 9                  -> ||A||_inf = 9
+        ||x||_inf = 2, ||b||_inf = 11             -> omega = 1 / (18 + 11) = 1/29
+
+    A largest-entry norm (6) would give 1/23 and a sum over all entries (22)
+    1/55; a residual of the wrong sign fails the rho check.
+    """
+    rp = np.array([0, 2, 5, 7], dtype=np.int32)
+    ci = np.array([0, 1, 0, 1, 2, 1, 2], dtype=np.int32)
+    v = np.array([4.0, -1.0, -2.0, 5.0, 1.0, 3.0, -6.0])
+    x = np.array([1.0, -2.0, 0.5])
+    b = np.array([7.0, -11.0, -8.0])
+    assert np.array_equal(oracle.residual(3, rp, ci, v, b, x), [1.0, 0.5, 1.0])
+    assert oracle.lib().orc_norm_inf_matrix(3, rp, v) == 9.0
+    assert oracle.omega(3, rp, ci, v, b, x) == 1.0 / 29.0
+    # through the pipeline object as well (its norm is computed once per value set)
+    o = oracle.Oracle(3, rp, ci, v, np.arange(3, dtype=np.int32))
+    assert o.anorm == 9.0 and o.omega(b, x) == 1.0 / 29.0
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_oracle_norm_inf_matches_dense_numpy(seed):
+    """||A||_inf of the oracle equals NumPy's dense matrix infinity norm (the
+    maximum absolute row sum).  Integer-valued entries make every sum exact, so
+    the comparison is exact; a largest-entry or all-entry mutation differs."""
+    n = 80
+    rp, ci = random_sparse_pattern(n, 0.06, seed)
+    v = np.random.default_rng(seed).integers(-9, 10, size=ci.size).astype(np.float64)
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n)).toarray()
+    ref = np.linalg.norm(A, np.inf)
+    assert oracle.lib().orc_norm_inf_matrix(n, rp, v) == ref
+    assert ref != np.abs(A).max() and ref != np.abs(A).sum()
+    # and omega against its definition written with NumPy's norms
+    x = np.random.default_rng(seed + 10).integers(-5, 6, size=n).astype(np.float64)
+    b = np.random.default_rng(seed + 20).integers(-50, 51, size=n).astype(np.float64)
+    rho = b - A @ x
+    want = np.linalg.norm(rho, np.inf) / (ref * np.linalg.norm(x, np.inf) + np.linalg.norm(b, np.inf))
+    assert oracle.omega(n, rp, ci, v, b, x) == want
