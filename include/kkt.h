@@ -301,13 +301,16 @@ kkt_status kkt_queue_status_sync(kkt_queue *q, kkt_stream stream, int *n_perturb
  * Scaled residual without any device allocation and without a context.
  *
  * The paper has no counterpart of this call; it exists for callers that cannot
- * allocate device memory where they need the residual: work recorded inside
- * CUDA stream capture (allocation is not allowed while a capture is active), or
- * programs that fix their device-memory budget at start-up.  Such callers may
- * not be able to create a kkt_ctx either, since kkt_analyze allocates.
+ * call cudaMalloc where they need the residual: programs that give their whole
+ * device-memory budget to their own pool allocator at start-up (a hidden
+ * allocation would fail or break the budget), and loops that cannot afford the
+ * device-wide synchronization that allocating and freeing can cause.  Such
+ * callers may not be able to create a kkt_ctx either, since kkt_analyze
+ * allocates.
  *
  * Computes rho = b - A x (FP64, same per-row arithmetic as kkt_refine) and
- *   out_dev[0] = omega = ||rho||_inf / (||A||_inf ||x||_inf + ||b||_inf),
+ *   out_dev[0] = omega = ||rho||_inf / (||A||_inf ||x||_inf + ||b||_inf)
+ *                (+infinity when any entry of x, b, rho or A is NaN or infinite),
  *   out_dev[1..4] = ||rho||_inf, ||x||_inf, ||b||_inf, ||A||_inf.
  *   n, row_ptr_dev[n+1], col_idx_dev[nnz], values_dev[nnz]: the matrix in CSR
  *   on the current device; b_dev, x_dev, rho_dev: n float64; out_dev: 5 float64.
@@ -315,11 +318,14 @@ kkt_status kkt_queue_status_sync(kkt_queue *q, kkt_stream stream, int *n_perturb
  *
  * Its only scratch is a fixed 4 MiB array compiled into the library (one
  * partial result per 32 rows), so n may not exceed 4,194,304: larger n returns
- * KKT_ERR_ARG and launches nothing.  The array's device address is looked up
- * the first time the call runs on a device, so make that first call before any
- * stream capture.  All calls on a device share the array and it keeps the last
- * call's contents; calls that overlap on the GPU race on it, so order them on
- * one stream.
+ * KKT_ERR_ARG and launches nothing.  A GPU commits the array when the library's
+ * device code is loaded on it -- with CUDA's lazy loading, at the latest during
+ * the first call on that device -- and keeps it until the process exits.  That
+ * first call also looks up the array's device address (once per device, with
+ * the device current), so make it before any stream capture.  All calls on a
+ * device share the array and it keeps the last call's contents; calls that
+ * overlap on the GPU race on it, so order them on one stream.  Failures set
+ * the text of kkt_last_error().
  */
 kkt_status kkt_scaled_residual_noalloc(int n, const int *row_ptr_dev, const int *col_idx_dev,
                                        const double *values_dev, const double *b_dev,

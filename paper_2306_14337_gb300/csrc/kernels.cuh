@@ -22,6 +22,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <string>
 
 namespace kkt {
 
@@ -98,6 +99,10 @@ struct RunCfg {
     int unpublished_row;         // failure-detection test: this row is never published (-1: none)
     unsigned poll_ns_max;        // backoff cap of a waiting lane (ns)
 };
+
+// Record the text returned by kkt_last_error() on the calling thread (every
+// translation unit of the library reports through this one store).
+void set_last_error(const std::string &msg);
 
 // Trace regions, one per phase, each (max work items) x 2 words.
 enum TracePhase { TR_REFACTOR = 0, TR_FWD = 1, TR_BWD = 2, TR_TFWD = 3, TR_TBWD = 4, TR_PHASES = 5 };

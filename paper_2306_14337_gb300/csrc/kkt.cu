@@ -94,6 +94,10 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double 
 
 __device__ __forceinline__ int floor_half(int e) { return e >= 0 ? e / 2 : -((1 - e) / 2); }
 
+// |v| for a max-reduction that must not lose NaN: fmax(NaN, y) = y would drop
+// a NaN entry from an infinity norm, so NaN counts as +infinity.
+__device__ __forceinline__ double abs_nan_inf(double v) { return isnan(v) ? INFINITY : fabs(v); }
+
 // ---------------------------------------------------------------------------
 // scaling and norms (8 lanes per row)
 
@@ -1391,9 +1395,9 @@ __global__ void k_resid(DevPattern P, const double *__restrict__ aval, const dou
         const double br = b[r];
         rv = br - acc;
         rho[r] = rv;
-        rv = fabs(rv);
-        xv = fabs(x[r]);
-        bv = fabs(br);
+        rv = abs_nan_inf(rv);
+        xv = abs_nan_inf(x[r]);
+        bv = abs_nan_inf(br);
     }
     for (int o = 16; o > 0; o >>= 1) {
         rv = fmax(rv, __shfl_xor_sync(FULL, rv, o));
@@ -1675,7 +1679,8 @@ __global__ void k_omega(const unsigned long long *__restrict__ norms, double *__
     const double bm = __longlong_as_double((long long)norms[NM_BMAX]);
     const double rm = __longlong_as_double((long long)norms[NM_RMAX]);
     const double den = an * xm + bm;
-    *out = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+    const double w = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+    *out = isnan(w) ? INFINITY : w;        // inf / inf: a non-finite entry somewhere
 }
 
 // rho = b - A x (or A^T x) per system, with per-system norms
@@ -1698,9 +1703,9 @@ __global__ void k_bresid(DevPattern P, int B, const double *__restrict__ aval, c
     const double br = b[gid];
     const double rv = br - acc;
     rho[gid] = rv;
-    atomic_max_nonneg(norms + (long long)NM_RMAX * B + sy, fabs(rv));
-    atomic_max_nonneg(norms + (long long)NM_XMAX * B + sy, fabs(x[gid]));
-    atomic_max_nonneg(norms + (long long)NM_BMAX * B + sy, fabs(br));
+    atomic_max_nonneg(norms + (long long)NM_RMAX * B + sy, abs_nan_inf(rv));
+    atomic_max_nonneg(norms + (long long)NM_XMAX * B + sy, abs_nan_inf(x[gid]));
+    atomic_max_nonneg(norms + (long long)NM_BMAX * B + sy, abs_nan_inf(br));
 }
 
 // dA_k = -lam[row_k] x[col_k]
@@ -1791,6 +1796,10 @@ struct kkt_ctx {
 };
 
 static thread_local std::string g_last_error;
+
+namespace kkt {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace kkt
 
 static kkt_status cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -2568,6 +2577,7 @@ static kkt_status residual_omega(kkt_ctx *c, const double *b, const double *x, i
     const double den = an * val(NM_XMAX) + val(NM_BMAX);
     const double r = val(NM_RMAX);
     *omega = den > 0 ? r / den : (r > 0 ? INFINITY : 0.0);
+    if (std::isnan(*omega)) *omega = INFINITY;   // inf / inf: a non-finite entry somewhere
     return KKT_OK;
 }
 
@@ -2738,6 +2748,9 @@ static kkt_status refine_any(kkt_ctx *c, const double *b, double *x, double tol,
     int dst[ST_WORDS];
     CK(cudaMemcpy(dst, c->d_status, sizeof(dst), cudaMemcpyDeviceToHost));
     if (dst[ST_TIMEOUT]) return KKT_ERR_TIMEOUT;
+    // a NaN or infinity in x, b or the residual (omega = inf), or one flagged
+    // earlier by the refactorization, makes the result unusable
+    if (!std::isfinite(w) || dst[ST_NONFINITE]) return KKT_ERR_NONFINITE;
     return (w <= tol) ? KKT_OK : KKT_ERR_NOT_CONVERGED;
 }
 
@@ -2877,6 +2890,7 @@ static kkt_status bresidual_omega(kkt_ctx *c, int B, const double *b, const doub
         const double den = an * val(NM_XMAX, sy) + val(NM_BMAX, sy);
         const double r = val(NM_RMAX, sy);
         omega[sy] = den > 0 ? r / den : (r > 0 ? INFINITY : 0.0);
+        if (std::isnan(omega[sy])) omega[sy] = INFINITY;
     }
     return KKT_OK;
 }
@@ -2906,6 +2920,7 @@ static kkt_status brefine_any(kkt_ctx *c, int B, const double *b, double *x, dou
     int dst[ST_WORDS];
     CK(cudaMemcpy(dst, c->d_status, sizeof(dst), cudaMemcpyDeviceToHost));
     if (dst[ST_TIMEOUT]) return KKT_ERR_TIMEOUT;
+    if (!std::isfinite(worst()) || dst[ST_NONFINITE]) return KKT_ERR_NONFINITE;
     return worst() <= tol ? KKT_OK : KKT_ERR_NOT_CONVERGED;
 }
 

@@ -1,21 +1,25 @@
 // noalloc.cu -- scaled residual of a CSR system without any device allocation.
 //
 // Who needs this: code that must not call cudaMalloc at the point where it
-// wants the residual.  Typical cases are work recorded inside CUDA stream
-// capture (allocating while a capture is active is not allowed), and
-// deployments that fix their whole device-memory budget when they start, where
-// a hidden allocation would break the budget.  Such callers may also be unable
-// to create a kkt_ctx, because kkt_analyze allocates the context's workspace.
-// This entry point needs neither: the caller passes the matrix, the vectors and
-// the outputs, and the only scratch is a fixed array compiled into the library.
+// wants the residual.  Typical cases are deployments that hand their whole
+// device-memory budget to their own pool allocator when they start (a hidden
+// cudaMalloc would fail or break the budget), and loops that cannot afford the
+// device-wide synchronization a cudaMalloc/cudaFree pair can cause.  Such
+// callers may also be unable to create a kkt_ctx, because kkt_analyze allocates
+// the context's workspace.  This entry point needs neither: the caller passes
+// the matrix, the vectors and the outputs, and the only scratch is a fixed
+// array compiled into the library.
 //
 // Scratch: one file-scope __device__ array, kNoallocMaxBlocks x 4 doubles
 // (4 MiB), holding one partial result per thread block of the residual pass.
-// Every GPU that loads the library holds it until the process exits.  All calls
-// on a device share it and it keeps the last call's contents; each call writes
-// every partial it later reads, so nothing has to start at zero.  Calls whose
-// execution overlaps on the GPU (different streams without ordering) race on
-// the array and must be avoided.
+// It belongs to the library's device code, so a GPU commits it when that code
+// is loaded on it (with CUDA's lazy module loading: at the latest during the
+// first call on that device, whose set-up looks the array's address up) and
+// holds it until the process exits.  All calls on a device share it and it
+// keeps the last call's contents; each call writes every partial it later
+// reads, so nothing has to start at zero.  Calls whose execution overlaps on
+// the GPU (different streams without ordering) race on the array and must be
+// avoided.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -24,6 +28,7 @@
 #include <string>
 
 #include "kkt.h"
+#include "kernels.cuh"
 
 namespace {
 
@@ -41,7 +46,9 @@ static __device__ __align__(256) double g_partials[kNoallocMaxBlocks * 4];
 std::mutex g_mu;
 double *g_addr[kMaxDevices] = {};
 
-thread_local std::string g_err;
+// NaN counts as +infinity in the maxima below: fmax(NaN, y) = y would drop a
+// NaN entry from a norm and report a small omega for a broken solution.
+__device__ __forceinline__ double abs_nan_inf(double v) { return isnan(v) ? INFINITY : fabs(v); }
 
 // Residual pass: rho = b - A x with 8 lanes per row (the same per-row
 // arithmetic as the library's refinement residual), and per-block maxima.
@@ -70,10 +77,10 @@ k_resid_partials(int n, const int *__restrict__ rp, const int *__restrict__ ci,
         const double br = b[r];
         const double rv = br - acc;
         rho[r] = rv;
-        v[0] = fabs(rv);
-        v[1] = fabs(x[r]);
-        v[2] = fabs(br);
-        v[3] = asum;
+        v[0] = abs_nan_inf(rv);
+        v[1] = abs_nan_inf(x[r]);
+        v[2] = abs_nan_inf(br);
+        v[3] = isnan(asum) ? INFINITY : asum;
     }
     for (int k = 0; k < 4; k++)
         for (int o = 16; o > 0; o >>= 1) v[k] = fmax(v[k], __shfl_xor_sync(FULL, v[k], o));
@@ -106,7 +113,8 @@ k_resid_finish(int nblocks, const double *__restrict__ partials, double *__restr
         for (int q = 0; q < kThreads / 32; q++)
             for (int k = 0; k < 4; k++) m[k] = fmax(m[k], red[q][k]);
         const double den = m[3] * m[1] + m[2];
-        out[0] = den > 0.0 ? m[0] / den : (m[0] > 0.0 ? INFINITY : 0.0);
+        const double w = den > 0.0 ? m[0] / den : (m[0] > 0.0 ? INFINITY : 0.0);
+        out[0] = isnan(w) ? INFINITY : w;     // inf / inf: a non-finite entry somewhere
         out[1] = m[0];
         out[2] = m[1];
         out[3] = m[2];
@@ -122,7 +130,7 @@ kkt_status scratch_address(int dev, double **out) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
         if (e != cudaSuccess) {
-            g_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            kkt::set_last_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             return KKT_ERR_CUDA;
         }
         g_addr[dev] = static_cast<double *>(p);
@@ -141,18 +149,34 @@ kkt_status kkt_scaled_residual_noalloc(int n, const int *row_ptr_dev, const int 
         !out_dev)
         return KKT_ERR_ARG;
     const long long nblocks = ((long long)n + kRowsPerBlock - 1) / kRowsPerBlock;
-    if (nblocks > kNoallocMaxBlocks) return KKT_ERR_ARG;   // n above 4,194,304 rows
+    if (nblocks > kNoallocMaxBlocks) {
+        kkt::set_last_error("kkt_scaled_residual_noalloc: n exceeds 4,194,304 rows");
+        return KKT_ERR_ARG;
+    }
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KKT_ERR_CUDA;
+    if (e != cudaSuccess) {
+        kkt::set_last_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+        return KKT_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        kkt::set_last_error("kkt_scaled_residual_noalloc: device ordinal above 63");
+        return KKT_ERR_CUDA;
+    }
     double *partials = nullptr;
     kkt_status st = scratch_address(dev, &partials);
     if (st != KKT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     k_resid_partials<<<(int)nblocks, kThreads, 0, s>>>(n, row_ptr_dev, col_idx_dev, values_dev, b_dev,
                                                         x_dev, rho_dev, partials);
-    if ((e = cudaGetLastError()) != cudaSuccess) return KKT_ERR_CUDA;
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        kkt::set_last_error(std::string("k_resid_partials launch: ") + cudaGetErrorString(e));
+        return KKT_ERR_CUDA;
+    }
     k_resid_finish<<<1, kThreads, 0, s>>>((int)nblocks, partials, out_dev);
-    if ((e = cudaGetLastError()) != cudaSuccess) return KKT_ERR_CUDA;
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        kkt::set_last_error(std::string("k_resid_finish launch: ") + cudaGetErrorString(e));
+        return KKT_ERR_CUDA;
+    }
     return KKT_OK;
 }

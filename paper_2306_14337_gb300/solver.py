@@ -170,7 +170,7 @@ class KKTSolver:
         st = fn(self._h, _ptr(b), _ptr(x), float(tol), int(max_it), C.byref(info), _stream(stream))
         if raise_on_fail:
             check(st, "kkt_refine")
-        elif st not in (_capi.KKT_OK, _capi.KKT_ERR_NOT_CONVERGED):
+        elif st not in (_capi.KKT_OK, _capi.KKT_ERR_NOT_CONVERGED, _capi.KKT_ERR_NONFINITE):
             check(st, "kkt_refine")
         return dict(status=st, iters=info.iters, converged=bool(info.converged), omega=info.omega,
                     history=list(info.omega_hist[: info.n_hist]))
@@ -224,7 +224,7 @@ class KKTSolver:
         it = C.c_int(0)
         st = fn(self._h, B, _ptr(b), _ptr(x), float(tol), int(max_it),
                 om.ctypes.data_as(C.POINTER(C.c_double)), C.byref(it), _stream(stream))
-        if st not in (_capi.KKT_OK, _capi.KKT_ERR_NOT_CONVERGED):
+        if st not in (_capi.KKT_OK, _capi.KKT_ERR_NOT_CONVERGED, _capi.KKT_ERR_NONFINITE):
             check(st, "kkt_batch_refine")
         return dict(status=st, iters=it.value, omega=om, converged=bool(np.all(om <= (tol or 1e-14))))
 
@@ -250,7 +250,9 @@ class _KKTSolveFn(torch.autograd.Function):
     def forward(ctx, solver: KKTSolver, values, b, tol, max_it):
         solver.refactor(values)
         x = solver.solve(b)
-        info = solver.refine(b, x, tol, max_it)
+        # a missed target or a non-finite solution raises (KKTError) instead of
+        # returning an x that does not solve the system
+        info = solver.refine(b, x, tol, max_it, raise_on_fail=True)
         ctx.solver = solver
         ctx.version = solver.version
         ctx.tol, ctx.max_it = tol, max_it
@@ -266,7 +268,7 @@ class _KKTSolveFn(torch.autograd.Function):
             solver.refactor(values)
         g = g.contiguous()
         lam = solver.solve_transpose(g)
-        solver.refine_transpose(g, lam, ctx.tol, ctx.max_it)
+        solver.refine_transpose(g, lam, ctx.tol, ctx.max_it, raise_on_fail=True)
         dA = solver.adjoint_gather(lam, x)
         return None, dA, lam, None, None
 

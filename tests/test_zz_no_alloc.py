@@ -1,9 +1,10 @@
 """The allocation-free scaled residual (kkt_scaled_residual_noalloc).
 
-That entry point serves callers that cannot allocate device memory where they
-need a residual, e.g. work recorded inside CUDA stream capture or programs
-that fix their device-memory budget at start-up; it uses a fixed scratch array
-compiled into the library instead of a context.  Here it is checked, through
+That entry point serves callers that cannot call cudaMalloc where they need a
+residual, e.g. programs that hand their whole device-memory budget to their
+own pool allocator at start-up, or loops that cannot afford the device-wide
+synchronization of an allocation; it uses a fixed scratch array compiled into
+the library instead of a context.  Here it is checked, through
 the C interface, against the context-based residual that kkt_refine reports
 (max_it = 0 evaluates omega for the given x without changing it), on two
 calls in a row so that contents left in the shared scratch by the first call
@@ -65,3 +66,32 @@ def test_noalloc_residual_rejects_sizes_beyond_its_scratch():
     d = C.c_void_p(16)                  # never dereferenced: the size check comes first
     st = L.kkt_scaled_residual_noalloc(4_194_305, d, d, d, d, d, d, d, C.c_void_p(0))
     assert st == _capi.KKT_ERR_ARG
+    assert b"4,194,304" in L.kkt_last_error()
+
+
+def test_noalloc_residual_reports_nan_as_infinite_omega():
+    """A NaN in x must not drop out of ||x||_inf or ||rho||_inf: omega is +inf,
+    as the context's refinement reports it (KKT_ERR_NONFINITE)."""
+    s = config_sequence(0)
+    v, b = s.values(2), s.rhs(2)
+    n = s.n
+    vt = torch.tensor(v, dtype=torch.float64, device=DEV)
+    bt = torch.tensor(b, dtype=torch.float64, device=DEV)
+    rp = torch.tensor(s.indptr, dtype=torch.int32, device=DEV)
+    ci = torch.tensor(s.indices, dtype=torch.int32, device=DEV)
+    S = KKTSolver(n, s.indptr, s.indices)
+    S.refactor(vt)
+    x = S.solve(bt)
+    S.refine(bt, x)
+    x[n // 2] = float("nan")
+    L = _capi.load()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rho = torch.empty(n, dtype=torch.float64, device=DEV)
+    out = torch.zeros(5, dtype=torch.float64, device=DEV)
+    assert L.kkt_scaled_residual_noalloc(n, _p(rp), _p(ci), _p(vt), _p(bt), _p(x), _p(rho), _p(out),
+                                         stream) == _capi.KKT_OK
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert o[0] == np.inf and o[2] == np.inf
+    r = S.refine(bt, x.clone(), tol=1e-14, max_it=0)
+    assert r["status"] == _capi.KKT_ERR_NONFINITE and r["omega"] == np.inf
