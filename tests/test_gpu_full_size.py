@@ -1,0 +1,105 @@
+"""Oracle parity at the full sizes of the three large workloads.
+
+* 10,000-bus x 64 scenarios, batched FP64 (KKT dimension 70,000);
+* 70,000-bus late-IPM system, FP32 factors + FP64 refinement (n = 490,000);
+* 48 uneven systems (16 x 500, 16 x 2,000, 12 x 5,000, 4 x 20,000 buses),
+  FP32 factors in one work queue + FP64 refinement, plus transposed solves.
+
+Factor entries are compared with the oracle's (Gilbert-Peierls LU with the
+same ordering, taken from the oracle's own minimum degree) at the tolerance
+of the other parity tests: |gpu - ref| <= max(rel |ref|, 4 E), E the oracle's
+running error bound, rel = 1e-11 with u = 2^-53 (FP64) or 1e-5 with E scaled
+to u = 2^-24 (FP32).  Solutions are run in the benchmark's configuration (the
+library's own ordering) and their scaled residual is recomputed by the oracle
+on the CPU: omega <= 1e-14 (Sec. 5.3 tolerance).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from kktgen import config_sequence
+from kktgen.acopf import uneven_sequences
+from paper_2306_14337_gb300 import KKTQueue, KKTSolver
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+def _check_factor(got, o, fp32):
+    rp, ci, ref, E = o.F.lu_csr()
+    assert got.shape == ref.shape
+    d = np.abs(got - ref)
+    tol = np.maximum(1e-5 * np.abs(ref), 4 * E * 2.0 ** 29) if fp32 else np.maximum(1e-11 * np.abs(ref), 4 * E)
+    bad = np.nonzero(~(d <= tol))[0]
+    assert bad.size == 0, f"{bad.size} of {d.size} entries off; worst {np.max(d[bad] / tol[bad]):.3g} x tol"
+
+
+def test_batched_10000bus_x64_factors_and_omega():
+    s = config_sequence(2)
+    k, B = 2, 64
+    vals = np.stack([s.values(k, sc) for sc in range(1, B + 1)], axis=1)
+    bs = np.stack([s.csr(k, sc) @ s.x_true(k, sc) for sc in range(1, B + 1)], axis=1)
+    vt, bt = torch.tensor(vals, device=DEV), torch.tensor(bs, device=DEV)
+    # factors of three scenarios of the batch, with the oracle's ordering
+    p = oracle.min_degree(s.n, s.indptr, s.indices)
+    Sp = KKTSolver(s.n, s.indptr, s.indices, perm=p, max_batch=B)
+    Sp.batch_refactor(vt)
+    for sc in (0, 31, 63):
+        o = oracle.Oracle(s.n, s.indptr, s.indices, vals[:, sc], p)
+        _check_factor(Sp.batch_export_factors(sc).cpu().numpy(), o, False)
+    del Sp
+    # the benchmark's configuration: every scenario refined, omega by the oracle
+    S = KKTSolver(s.n, s.indptr, s.indices, max_batch=B)
+    S.batch_refactor(vt)
+    x = S.batch_solve(bt)
+    info = S.batch_refine(bt, x, 1e-14, 40)
+    xh = x.cpu().numpy()
+    w = [oracle.omega(s.n, s.indptr, s.indices, vals[:, sc], bs[:, sc], xh[:, sc]) for sc in range(B)]
+    assert max(w) <= 1e-14, (max(w), info["iters"])
+
+
+def test_70000bus_fp32_factors_and_refined_omega():
+    s = config_sequence(3)
+    v, b = s.values(0), s.rhs(0)
+    vt, bt = torch.tensor(v, device=DEV), torch.tensor(b, device=DEV)
+    p = oracle.min_degree(s.n, s.indptr, s.indices)
+    S = KKTSolver(s.n, s.indptr, s.indices, perm=p, fp32=True)
+    S.refactor(vt)
+    o = oracle.Oracle(s.n, s.indptr, s.indices, v, p, tau_rel=2.0 ** -24)
+    assert S.status()[1] == o.F.n_perturbed
+    _check_factor(S.export_factors().cpu().numpy(), o, True)
+    del S, o
+    # the benchmark's configuration: library ordering, FP32 factors, FP64 refinement
+    S = KKTSolver(s.n, s.indptr, s.indices, fp32=True, refine_mode="auto")
+    S.refactor(vt)
+    x = S.solve(bt)
+    info = S.refine(bt, x, 1e-14, 20)
+    assert info["converged"], info
+    assert oracle.omega(s.n, s.indptr, s.indices, v, b, x.cpu().numpy()) <= 1e-14
+
+
+def test_uneven_48_queue_omega_and_transposed():
+    seqs = uneven_sequences()
+    assert len(seqs) == 48
+    sols = [KKTSolver(q.n, q.indptr, q.indices, fp32=True, refine_mode="auto") for q in seqs]
+    Q = KKTQueue(sols)
+    vals = [torch.tensor(q.values(0), device=DEV) for q in seqs]
+    bs = [torch.tensor(q.rhs(0), device=DEV) for q in seqs]
+    xs = [torch.zeros_like(b) for b in bs]
+    om = torch.zeros(len(seqs), dtype=torch.float64, device=DEV)
+    Q.run(vals, bs, xs, n_refine=8, omega=om)
+    torch.cuda.synchronize()
+    gs = [torch.tensor(np.random.default_rng(k).standard_normal(q.n), device=DEV) for k, q in enumerate(seqs)]
+    lams = [torch.zeros_like(g) for g in gs]
+    Q.solve_transpose(gs, lams)
+    for k, q in enumerate(seqs):
+        if not (om[k].item() <= 1e-14):
+            sols[k].refine(bs[k], xs[k], 1e-14, 20)
+        sols[k].refine_transpose(gs[k], lams[k], 1e-14, 20)
+        v = q.values(0)
+        w = oracle.omega(q.n, q.indptr, q.indices, v, q.rhs(0), xs[k].cpu().numpy())
+        assert w <= 1e-14, (k, q.n, w)
+        At = q.csr(0).T.tocsr()
+        wt = oracle.omega(q.n, At.indptr, At.indices, At.data, gs[k].cpu().numpy(), lams[k].cpu().numpy())
+        assert wt <= 1e-14, (k, q.n, wt)

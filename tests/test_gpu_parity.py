@@ -75,15 +75,34 @@ def test_refactor_parity_200bus(step, equil):
 
 
 @pytest.mark.parametrize("step", [0, 29])
-def test_refactor_parity_2000bus(step):
+@pytest.mark.parametrize("budget", [0, 1])
+def test_refactor_parity_2000bus(step, budget):
+    """budget = 1 byte leaves the update maps out, so every update target is
+    found by the binary search of the row's sorted columns (the path that
+    systems whose maps exceed the budget take)."""
     s = _seq(1)
     p = _perm(s, ("cfg1",))
     v = s.values(step)
-    S = KKTSolver(s.n, s.indptr, s.indices, perm=p)
+    S = KKTSolver(s.n, s.indptr, s.indices, perm=p, update_map_budget=budget)
+    assert (S.stats()["update_map_entries"] == 0) == (budget == 1)
     o = oracle.Oracle(s.n, s.indptr, s.indices, v, p)
     S.refactor(_t(v))
     assert S.status()[1] == o.F.n_perturbed
     _check_factors(S, o)
+
+
+@pytest.mark.parametrize("equil", [True, False])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_refactor_parity_200bus_without_update_maps(equil, fp32):
+    s = _seq(0, asym=0.1)
+    p = _perm(s, ("cfg0",))
+    v = s.values(9)
+    S = KKTSolver(s.n, s.indptr, s.indices, perm=p, equilibrate=equil, fp32=fp32, update_map_budget=1)
+    assert S.stats()["update_map_entries"] == 0
+    o = oracle.Oracle(s.n, s.indptr, s.indices, v, p, equil=equil, tau_rel=2.0 ** -24 if fp32 else 1e-14)
+    S.refactor(_t(v))
+    assert S.status()[1] == o.F.n_perturbed
+    _check_factors(S, o, fp32=fp32)
 
 
 def test_contexts_of_different_sizes_coexist():
@@ -372,15 +391,16 @@ def test_rows_longer_than_shared_memory():
     rp[1:] = np.cumsum([len(np.unique(r)) for r in rows])
     ci = np.concatenate([np.unique(r) for r in rows]).astype(np.int32)
     v = random_dd_values(rp, ci, 4)
-    S = KKTSolver(n, rp, ci, ordering="natural")
-    assert S.stats()["max_row"] > 1024
-    S.refactor(_t(v))
     o = oracle.Oracle(n, rp, ci, v, np.arange(n, dtype=np.int32))
-    _check_factors(S, o)
     b = np.random.default_rng(0).standard_normal(n)
-    x = S.solve(_t(b))
-    S.refine(_t(b), x)
-    assert oracle.omega(n, rp, ci, v, b, x.cpu().numpy()) <= 1e-14
+    for budget in (0, 1):                # with and without the update maps
+        S = KKTSolver(n, rp, ci, ordering="natural", update_map_budget=budget)
+        assert S.stats()["max_row"] > 1024
+        S.refactor(_t(v))
+        _check_factors(S, o)
+        x = S.solve(_t(b))
+        S.refine(_t(b), x)
+        assert oracle.omega(n, rp, ci, v, b, x.cpu().numpy()) <= 1e-14
 
 
 @pytest.mark.parametrize("n,density,seed", [(2, 1.0, 1), (33, 0.2, 2), (257, 0.02, 3), (1000, 0.004, 4)])
