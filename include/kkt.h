@@ -98,6 +98,11 @@ typedef struct {
                                refactorization never publishes this row (numbered
                                like kkt_export_symbolic), so the rows that depend on
                                it exhaust spin_limit and report KKT_ERR_TIMEOUT */
+    int refactor_big_warps; /* warps per CTA of the refactorization that own a
+                               shared-memory row for the rows longer than 1,024
+                               entries (k > 0: k, at most half the CTA, as far as
+                               shared memory allows; 0 = none: such rows work in
+                               global scratch, the faster choice where measured) */
 } kkt_options;
 
 typedef struct {
@@ -123,6 +128,9 @@ typedef struct {
     long long update_map_entries; /* 0 when the update maps are not built */
     int n_tasks;            /* longest-path tasks of the triangular solves */
     int max_task;           /* rows in the longest task */
+    int refactor_big_warps; /* warps per CTA of the refactorization that take the
+                               rows longer than 1,024 entries (0: no such rows) */
+    int refactor_big_cap;   /* row capacity (entries) of those warps' shared memory */
 } kkt_stats;
 
 typedef struct {
@@ -296,6 +304,17 @@ kkt_status kkt_queue_run(kkt_queue *q, const double *const *values, const double
 kkt_status kkt_queue_solve_transpose(kkt_queue *q, const double *const *g, double *const *lam,
                                      kkt_stream stream);
 kkt_status kkt_queue_status_sync(kkt_queue *q, kkt_stream stream, int *n_perturbed);
+
+/*
+ * Measured fused multiply-add throughput of the device (TFLOP/s, 2 flops per
+ * FMA) in FP64 (fp64 = 1) or FP32 (fp64 = 0): every thread of 8 CTAs of 256
+ * per SM runs eight independent FMA chains; the best of five timed launches.
+ * The paper has no counterpart; it supplies the arithmetic roofline against
+ * which the benchmark states the refactorization's rate.  Synchronizes the
+ * device and allocates a small output buffer.  Errors: KKT_ERR_ARG,
+ * KKT_ERR_CUDA (text in kkt_last_error()).
+ */
+kkt_status kkt_probe_fma_tflops(int device, int fp64, double *tflops);
 
 /*
  * Scaled residual without any device allocation and without a context.

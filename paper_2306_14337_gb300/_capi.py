@@ -48,6 +48,7 @@ class Options(C.Structure):
         ("trace", C.c_int),
         ("poll_ns_max", C.c_int),
         ("unpublished_row", C.c_int),
+        ("refactor_big_warps", C.c_int),
     ]
 
 
@@ -75,6 +76,8 @@ class Stats(C.Structure):
         ("update_map_entries", C.c_longlong),
         ("n_tasks", C.c_int),
         ("max_task", C.c_int),
+        ("refactor_big_warps", C.c_int),
+        ("refactor_big_cap", C.c_int),
     ]
 
 
@@ -125,6 +128,7 @@ SIGNATURES = {
     "kkt_queue_solve_transpose": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), _vp]),
     "kkt_queue_status_sync": (C.c_int, [_vp, _vp, _ip]),
     "kkt_scaled_residual_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "kkt_probe_fma_tflops": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
 }
 
 _lib = None

@@ -35,10 +35,12 @@ enum NormSlot { NM_ANORM = 0, NM_A1NORM = 1, NM_AMAX = 2, NM_RMAX = 3, NM_XMAX =
                 NM_WORDS = 8 };
 
 struct Sched {
-    int next;   // row-claim counter
-    int done;   // warps that found the queue empty
-    int epoch;  // epoch of the last completed triangular launch (shared by all phases)
-    int pad;
+    int next;       // row-claim counter (the refactorization: its free-row queue)
+    int done;       // warps that found the queue empty
+    int epoch;      // epoch of the last completed triangular launch (shared by all phases)
+    int next_long;  // claim counters of the refactorization's long-row and
+    int next_rest;  //   remaining-row queues
+    int pad[3];
 };
 
 struct DevPattern {
@@ -49,6 +51,12 @@ struct DevPattern {
     const int *perm, *iperm;             // new -> old, old -> new
     const int *lu_rp, *lu_ci, *diag, *src, *tpos;
     const int *order_f, *order_b;        // rows by forward / backward level
+    // The single-system refactorization splits order_f in three subsequences
+    // (see k_refactor): rows without a long descendant (order_free), rows
+    // longer than the small per-warp buffer (order_long), and the other rows
+    // (order_rest), of n_free / n_long / n - n_free - n_long rows.
+    const int *order_free, *order_long, *order_rest;
+    int n_free, n_long;
     const unsigned *upd_off;             // update maps (null when not built)
     const unsigned short *upd_map;
 };
@@ -92,6 +100,13 @@ struct RunCfg {
     unsigned long long *norms;   // NM_WORDS
     Sched *sched;                // one scheduler record per context (phases are stream-ordered)
     int cap;                     // shared-memory row capacity per warp of the refactorization
+                                 // (batched and queued kernels; small warps of k_refactor)
+    int cap_big;                 // k_refactor: row capacity of its big warps
+    int nbig;                    // k_refactor: big warps per CTA (warps 0 .. nbig-1; 0 = none)
+    int smem_cols;               // k_refactor: 1 if the row's columns are staged too (no update maps)
+    int staged;                  // k_refactor: 1 = pivot rows fed through each warp's staging ring
+    int warp_bytes_big;          // k_refactor: shared-memory bytes of a big / small warp's block
+    int warp_bytes_small;
     void *scratch;               // per-warp global rows for rows longer than cap
     int scratch_stride;          // entries per warp in scratch
     unsigned long long *trace;   // optional: per work item {claim, done} %globaltimer (ns)

@@ -82,6 +82,8 @@ __device__ __forceinline__ void finish_launch(const RunCfg &rc, int e) {
     int d = atomicAdd(&rc.sched->done, 1);
     if (d == total - 1) {
         rc.sched->next = 0;
+        rc.sched->next_long = 0;
+        rc.sched->next_rest = 0;
         rc.sched->done = 0;
         __threadfence();
         rc.sched->epoch = e;
@@ -300,16 +302,17 @@ template <typename T> struct Strided {
 // finished row is also written to the transposed layout (LUT[tpos[t]]) for
 // the transposed solves.
 // One row of the refactorization (the warp of lane `lane`); sval / scol are
-// the warp's shared-memory row of capacity rc.cap, gw its global warp index.
+// the warp's shared-memory row of capacity cap (scol is used only without
+// update maps), gw its global warp index (its global scratch row).
 template <typename T, typename AV = const double *, typename TP = T *>
 __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &rc, AV aval, AV sp, TP LU,
                                              TP LUT, TP rcp, double tau, int i, T *sval, int *scol,
-                                             int gw, int lane) {
+                                             int cap, int gw, int lane) {
     const bool mapped = P.upd_off != nullptr;
             const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
             const int *c = P.lu_ci + rb;
             T *w;
-            if (len <= rc.cap) {
+            if (len <= cap) {
                 w = sval;
                 if (!mapped) {
                     for (int t = lane; t < len; t += 32) scol[t] = c[t];
@@ -528,25 +531,276 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
             }
 }
 
+// ---------------------------------------------------------------------------
+// Staged pivot steps (single-system refactorization with update maps).
+//
+// A pivot step of row i reads U(d, >d) of its pivot row d and the relative
+// positions of those entries in row i (the update map).  Near the top of the
+// elimination tree a row takes thousands of pivot steps over pivot rows of
+// several hundred entries; loading each step's data when the step starts
+// exposes one memory round trip per block of the pivot row (measured: 2.5 us
+// per step in FP32, 3.9 us in FP64, on the 70,000-bus KKT).  Here the pivot
+// rows are cut into units of SB entries (one SB-entry block of one step), and
+// every warp keeps a ring of STAGES units in shared memory that cp.async fills
+// STAGES - 1 units ahead of the unit being applied: values and map targets in
+// 16-byte chunks (the copy starts at the 16-byte boundary below the block and
+// indexes from the remainder), the reciprocal pivot with the first block.
+// Values copied before their row was published hold the not-ready marker and
+// are reloaded from global memory (marker protocol above); the update maps
+// never change.
+template <typename T> struct Stage {
+    static constexpr int SB = sizeof(T) == 4 ? 256 : 128;       // entries per unit (32 x UJ)
+    static constexpr int VE = 16 / (int)sizeof(T);              // values per 16-byte chunk
+    static constexpr int STAGES = sizeof(T) == 4 ? 6 : 4;
+    static constexpr int VAL_BYTES = ((SB + VE) * (int)sizeof(T) + 15) / 16 * 16;
+    static constexpr int MAP_BYTES = ((SB + 8) * 2 + 15) / 16 * 16;
+    static constexpr int SLOT = VAL_BYTES + MAP_BYTES + 16 + 32;  // + reciprocal pivot + descriptor
+    static constexpr int RING = STAGES * SLOT;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_word(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_word(double *dst, const double *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Row i of the refactorization as refactor_row, with the pivot steps fed from
+// the warp's staging ring (shared memory, Stage<T>::RING bytes).  Requires the
+// update maps.  LU and the update map must be readable 16 bytes past their
+// ends (the last chunk of a block is rounded up).
+template <typename T>
+__device__ __forceinline__ void refactor_row_staged(const DevPattern &P, const RunCfg &rc,
+                                                    const double *__restrict__ aval,
+                                                    const double *__restrict__ sp, T *LU, T *LUT, T *rcp,
+                                                    double tau, int i, T *sval, int cap,
+                                                    unsigned char *ring, int gw, int lane) {
+    using S = Stage<T>;
+    constexpr int UJ = S::SB / 32;
+    const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
+    T *w = len <= cap ? sval : reinterpret_cast<T *>(rc.scratch) + (size_t)gw * rc.scratch_stride;
+    const double si = sp[i];
+    for (int t = lane; t < len; t += 32) {
+        const int k = P.src[rb + t];
+        w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + t]] * aval[k] : 0.0);
+    }
+    __syncwarp();
+    if (dp > 0) {
+        // producer: next unit to stage is block pb of step pt; the metadata of
+        // steps c0 .. c0 + 31 (lane k: step c0 + k) and of the chunk after it
+        int pt = 0, pb = 0, c0 = 0;
+        int md = 0, mub = 0, mue = 0, nd = 0, nub = 0, nue = 0;
+        unsigned mmo = 0, nmo = 0;
+        auto load_meta = [&](int t0, int &d_, int &ub_, int &ue_, unsigned &mo_) {
+            d_ = ub_ = ue_ = 0;
+            mo_ = 0;
+            if (t0 + lane < dp) {
+                d_ = P.lu_ci[rb + t0 + lane];
+                ub_ = P.diag[d_];
+                ue_ = P.lu_rp[d_ + 1];
+                mo_ = P.upd_off[rb + t0 + lane];
+            }
+        };
+        load_meta(0, md, mub, mue, mmo);
+        load_meta(32, nd, nub, nue, nmo);
+        auto issue = [&](int unit) {
+            unsigned char *slot = ring + (unit % S::STAGES) * S::SLOT;
+            if (pt < dp) {
+                if (pt - c0 >= 32) {                    // next metadata chunk
+                    c0 += 32;
+                    md = nd; mub = nub; mue = nue; mmo = nmo;
+                    load_meta(c0 + 32, nd, nub, nue, nmo);
+                }
+                const int k = pt - c0;
+                const int d = __shfl_sync(FULL, md, k), ub = __shfl_sync(FULL, mub, k);
+                const int ue = __shfl_sync(FULL, mue, k);
+                const unsigned mo = __shfl_sync(FULL, mmo, k);
+                const int u0 = ub + 1 + pb * S::SB;
+                const int cnt = min(S::SB, ue - u0);
+                const int last = (u0 + S::SB >= ue);
+                const int vo = u0 & (S::VE - 1);
+                const unsigned mstart = mo + (unsigned)(u0 - ub - 1);
+                const int mo2 = (int)(mstart & 7u);
+                T *sv = reinterpret_cast<T *>(slot);
+                unsigned short *sm = reinterpret_cast<unsigned short *>(slot + S::VAL_BYTES);
+                T *sr = reinterpret_cast<T *>(slot + S::VAL_BYTES + S::MAP_BYTES);
+                int *desc = reinterpret_cast<int *>(slot + S::VAL_BYTES + S::MAP_BYTES + 16);
+                const T *vsrc = LU + (u0 - vo);
+                const int vch = (vo + cnt + S::VE - 1) / S::VE;
+                for (int q = lane; q < vch; q += 32) cp_async16(sv + q * S::VE, vsrc + q * S::VE);
+                const unsigned short *msrc = P.upd_map + (mstart - (unsigned)mo2);
+                const int mch = (mo2 + cnt + 7) / 8;
+                for (int q = lane; q < mch; q += 32) cp_async16(sm + q * 8, msrc + q * 8);
+                if (pb == 0 && lane == 0) cp_async_word(sr, rcp + d);
+                if (lane == 0) {
+                    desc[0] = pt; desc[1] = u0; desc[2] = cnt; desc[3] = vo;
+                    desc[4] = mo2; desc[5] = d; desc[6] = (pb == 0) | (last << 1);
+                }
+                if (last) { pt++; pb = 0; } else { pb++; }
+            }
+            cp_async_commit();                          // an empty group past the last unit
+        };
+        for (int q = 0; q < S::STAGES - 1; q++) issue(q);
+        T l = T(0);
+        for (int unit = 0;; unit++) {
+            __syncwarp();                               // the slot issued next was consumed
+            issue(unit + S::STAGES - 1);
+            cp_async_wait<S::STAGES - 1>();
+            __syncwarp();                               // every lane's copies of this unit landed
+            unsigned char *slot = ring + (unit % S::STAGES) * S::SLOT;
+            const T *sv = reinterpret_cast<const T *>(slot);
+            const unsigned short *sm = reinterpret_cast<const unsigned short *>(slot + S::VAL_BYTES);
+            const T *sr = reinterpret_cast<const T *>(slot + S::VAL_BYTES + S::MAP_BYTES);
+            const int *desc = reinterpret_cast<const int *>(slot + S::VAL_BYTES + S::MAP_BYTES + 16);
+            const int t = desc[0], u0 = desc[1], cnt = desc[2], vo = desc[3], mo2 = desc[4], d = desc[5];
+            const int flags = desc[6];
+            if (flags & 1) {                            // first block: the multiplier
+                T r = sr[0];
+                if (is_marker(r)) {
+                    r = ld_relaxed_v(rcp + d);
+                    if (__any_sync(FULL, lane == 0 && is_marker(r))) {
+                        const T w0 = warp_wait_load(rc, rcp + d, lane == 0, lane);
+                        if (lane == 0) r = w0;
+                    }
+                    r = __shfl_sync(FULL, r, 0);
+                }
+                l = w[t] * r;
+            }
+            int lo[UJ];
+            T uv[UJ];
+            unsigned need = 0;
+#pragma unroll
+            for (int q = 0; q < UJ; q++) {
+                const int j = 32 * q + lane;
+                lo[q] = -1;
+                uv[q] = T(0);
+                if (j < cnt) {
+                    lo[q] = sm[mo2 + j];
+                    uv[q] = sv[vo + j];
+                    if (is_marker(uv[q])) need |= 1u << q;
+                }
+            }
+            if (__any_sync(FULL, need != 0)) {          // copied before publication: reload once,
+#pragma unroll                                          // then wait per entry
+                for (int q = 0; q < UJ; q++)
+                    if ((need >> q) & 1u) uv[q] = ld_relaxed_v(LU + (u0 + 32 * q + lane));
+                need = 0;
+#pragma unroll
+                for (int q = 0; q < UJ; q++)
+                    if (lo[q] >= 0 && is_marker(uv[q])) need |= 1u << q;
+                if (__any_sync(FULL, need != 0)) {
+#pragma unroll
+                    for (int q = 0; q < UJ; q++) {
+                        const bool nq = (need >> q) & 1u;
+                        const T v = warp_wait_load(rc, LU + (nq ? u0 + 32 * q + lane : u0), nq, lane);
+                        if (nq) uv[q] = v;
+                    }
+                }
+            }
+            // the block's targets are distinct: all loads, then all updates
+            T x[UJ];
+#pragma unroll
+            for (int q = 0; q < UJ; q++) x[q] = lo[q] >= 0 ? w[lo[q]] : T(0);
+#pragma unroll
+            for (int q = 0; q < UJ; q++)
+                if (lo[q] >= 0) w[lo[q]] = x[q] - l * uv[q];
+            if (flags & 2) {                            // last block of step t
+                __syncwarp();
+                if (lane == 0) w[t] = l;
+                if (t + 1 == dp) break;
+            }
+        }
+        cp_async_wait<0>();                             // nothing of this row left in flight
+        __syncwarp();
+    }
+    // pivot test in FP64 (perturb to sign(a_ii) tau and count)
+    if (lane == 0) {
+        double pv = (double)w[dp];
+        if (!(fabs(pv) >= tau) || isinf(pv)) {
+            const int k = P.src[rb + dp];
+            const double aii = (k >= 0) ? si * si * aval[k] : 0.0;
+            if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
+            pv = (aii < 0.0) ? -tau : tau;
+            atomicAdd(rc.status + ST_PERTURBED, 1);
+        }
+        w[dp] = (T)pv;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        LU[rb + dp] = w[dp];
+        if (i != rc.unpublished_row) publish(rc, rcp + i, T(1) / w[dp]);
+    }
+    for (int t = dp + 1 + lane; t < len; t += 32) publish(rc, LU + (rb + t), w[t]);
+    for (int t = lane; t < len; t += 32) {
+        if (t < dp) LU[rb + t] = w[t];
+        LUT[P.tpos[rb + t]] = w[t];
+    }
+}
+
+// Shared memory of k_refactor: warps 0 .. nbig-1 of every CTA ("big" warps)
+// own a row buffer of cap_big entries, the others one of cap entries; the
+// rows' columns follow in a second region of the same shape when there are no
+// update maps.  Rows longer than cap (the top of the elimination tree, whose
+// thousands of pivot steps would otherwise run against global memory) go to
+// big warps only.  Three queues, each a subsequence of the deepest-first
+// order: "free" rows (no long row below them in the tree, so they wait only
+// on free rows), long rows, and the rest.  Every warp drains the free queue
+// first (big warps help with the bulk of the tree), then big warps take long
+// rows, then everyone takes the rest.  Deadlock-free: take the earliest
+// unfinished row r.  Every row before r in r's queue is finished, and each
+// warp holds one row at a time; a warp holding a row from a later queue
+// entered that queue only after r's queue was fully claimed (free before
+// long before rest, and small warps never take long rows), and a warp still
+// in an earlier queue finishes its row -- a free row waits only on free rows,
+// a long row on rows before it -- so some warp eligible for r's queue
+// becomes free and claims r.
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32, 2)
 k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const double *__restrict__ sp,
            T *LU, T *LUT, T *rcp, double tau_rel) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T *sval = reinterpret_cast<T *>(smem) + (size_t)wid * rc.cap;
-    int *scol = reinterpret_cast<int *>(smem + (size_t)nw * rc.cap * sizeof(T)) + (size_t)wid * rc.cap;
+    // per-warp block: row values [cap], columns [cap] (no update maps), staging ring
+    const bool big = wid < rc.nbig;
+    const int cap = big ? rc.cap_big : rc.cap;
+    unsigned char *mine = smem + (big ? (size_t)wid * rc.warp_bytes_big
+                                      : (size_t)rc.nbig * rc.warp_bytes_big +
+                                            (size_t)(wid - rc.nbig) * rc.warp_bytes_small);
+    T *sval = reinterpret_cast<T *>(mine);
+    const size_t vb = ((size_t)cap * sizeof(T) + 15) & ~(size_t)15;
+    int *scol = rc.smem_cols ? reinterpret_cast<int *>(mine + vb) : nullptr;
+    unsigned char *ring = rc.staged ? mine + vb : nullptr;
     const int e = rc.sched->epoch + 1;
     const int gw = blockIdx.x * nw + wid;
     const double tau = tau_rel * __longlong_as_double((long long)rc.norms[NM_AMAX]);
-    for (;;) {
-        const int slot = claim_row(rc, lane);
-        if (slot >= P.n) break;
-        const int row = P.order_f[slot];
-        trace_mark(rc, 0, row, 0, lane);
-        refactor_row<T>(P, rc, aval, sp, LU, LUT, rcp, tau, row, sval, scol, gw, lane);
-        trace_mark(rc, 0, row, 1, lane);
-    }
+    auto drain = [&](int *counter, const int *order, int count) {
+        for (;;) {
+            int slot = 0;
+            if (lane == 0) slot = atomicAdd(counter, 1);
+            slot = __shfl_sync(FULL, slot, 0);
+            if (slot >= count) break;
+            const int row = order[slot];
+            trace_mark(rc, 0, row, 0, lane);
+            if (rc.staged)
+                refactor_row_staged<T>(P, rc, aval, sp, LU, LUT, rcp, tau, row, sval, cap, ring, gw, lane);
+            else
+                refactor_row<T>(P, rc, aval, sp, LU, LUT, rcp, tau, row, sval, scol, cap, gw, lane);
+            trace_mark(rc, 0, row, 1, lane);
+        }
+    };
+    drain(&rc.sched->next, P.order_free, P.n_free);
+    if (big) drain(&rc.sched->next_long, P.order_long, P.n_long);
+    drain(&rc.sched->next_rest, P.order_rest, P.n - P.n_free - P.n_long);
     if (lane == 0) finish_launch(rc, e);
 }
 
@@ -1554,7 +1808,7 @@ k_brefactor(DevPattern P, RunCfg rc, int B, const double *__restrict__ aval, con
         const double tau = tau_rel * __longlong_as_double((long long)norms[(long long)NM_AMAX * B + sy]);
         refactor_row<T>(P, rc, Strided<const double>{aval, B, sy}, Strided<const double>{sp, B, sy},
                         Strided<T>{LU, B, sy}, Strided<T>{LUT, B, sy}, Strided<T>{rcp, B, sy}, tau, i, sval,
-                        scol, gw, lane);
+                        scol, rc.cap, gw, lane);
     }
     if (lane == 0) finish_launch(rc, e);
 }
@@ -1619,7 +1873,7 @@ k_qrefactor(const QSys *__restrict__ sys, const int2 *__restrict__ items, int ni
         const QSys &q = sys[it.x];
         const double tau = q.tau_rel * __longlong_as_double((long long)q.norms[NM_AMAX]);
         refactor_row<T>(q.P, rc, q.values, q.sp, (T *)q.LU, (T *)q.LUT, (T *)q.rcp, tau, it.y, sval, scol,
-                        gw, lane);
+                        rc.cap, gw, lane);
     }
     if (lane == 0) finish_launch(rc, e);
 }
@@ -1785,6 +2039,8 @@ struct kkt_ctx {
     unsigned long long *h_norms = nullptr;  // pinned
     int grid = 0, solve_grid = 0, bsolve_grid = 0, cta_warps = WARPS, solve_warps = SWARPS, cap = 0;
     size_t smem = 0, device_bytes = 0;
+    int rgrid = 0;                   // CTAs of k_refactor
+    size_t rsmem = 0;                // shared memory of k_refactor (big and small warp rows)
     long long nnz_lu = 0;
     std::vector<int> at_rp, at_src;
     const double *values = nullptr;  // values of the current factorization (caller-owned)
@@ -1870,6 +2126,7 @@ void kkt_default_options(kkt_options *o) {
     o->trace = 0;
     o->unpublished_row = -1;
     o->poll_ns_max = 0;
+    o->refactor_big_warps = 0;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -1906,6 +2163,20 @@ static kkt_status upload(kkt_ctx *c) {
         std::vector<int> f(c->at_rp.begin(), c->at_rp.end() - 1);
         for (long long k = 0; k < nnza; k++) c->at_src[f[a.a_ci[k]]++] = (int)k;
     }
+    // claim queues of the single-system refactorization (see k_refactor):
+    // rows longer than the small per-warp buffer go to the big warps; rows
+    // with no such row below them in the elimination tree come first
+    const int cap_s = std::min(((std::max(a.max_row, 32) + 31) / 32) * 32, 1024);
+    std::vector<int> ord_free, ord_long, ord_rest;
+    {
+        std::vector<char> is_long(n), below(n, 0);      // below: a long row in the subtree, excluding itself
+        for (int r = 0; r < n; r++) is_long[r] = a.lu_rp[r + 1] - a.lu_rp[r] > cap_s;
+        for (int r = 0; r < n; r++)                      // children before parents (postorder labels)
+            if (a.parent[r] >= 0 && (below[r] || is_long[r])) below[a.parent[r]] = 1;
+        ord_free.reserve(n);
+        for (int r : a.order_f)
+            (is_long[r] ? ord_long : below[r] ? ord_rest : ord_free).push_back(r);
+    }
     struct Arr { const int *h; long long m; const int **dst; };
     std::vector<Arr> arrs = {
         {a.a_rp.data(), n + 1, &c->P.a_rp},     {a.a_ci.data(), nnza, &c->P.a_ci},
@@ -1915,6 +2186,9 @@ static kkt_status upload(kkt_ctx *c) {
         {a.lu_ci.data(), nlu, &c->P.lu_ci},     {a.diag.data(), n, &c->P.diag},
         {a.src.data(), nlu, &c->P.src},         {a.tpos.data(), nlu, &c->P.tpos},
         {a.order_f.data(), n, &c->P.order_f},   {a.order_b.data(), n, &c->P.order_b},
+        {ord_free.data(), (long long)ord_free.size(), &c->P.order_free},
+        {ord_long.data(), (long long)ord_long.size(), &c->P.order_long},
+        {ord_rest.data(), (long long)ord_rest.size(), &c->P.order_rest},
         {a.task_lo.data(), (long long)a.task_lo.size(), &c->tk.task_lo},
         {a.task_hi.data(), (long long)a.task_hi.size(), &c->tk.task_hi},
     };
@@ -1931,10 +2205,12 @@ static kkt_status upload(kkt_ctx *c) {
     c->device_bytes = total * sizeof(int);
     c->P.n = n;
     c->P.nnz_a = nnza;
+    c->P.n_free = (int)ord_free.size();
+    c->P.n_long = (int)ord_long.size();
 
     const bool f32 = c->opt.factor_fp32 != 0;
     const size_t tsz = f32 ? sizeof(float) : sizeof(double);
-    CK(cudaMalloc(&c->d_lu, nlu * tsz));
+    CK(cudaMalloc(&c->d_lu, nlu * tsz + 64));     // + 64: 16-byte copies may round up past the end
     CK(cudaMalloc(&c->d_lut, nlu * tsz));
     CK(cudaMalloc(&c->d_rcp, (size_t)n * tsz));
     CK(cudaMalloc(&c->d_s, n * sizeof(double)));
@@ -1956,10 +2232,9 @@ static kkt_status upload(kkt_ctx *c) {
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
     c->cta_warps = c->opt.cta_warps > 0 ? std::min(c->opt.cta_warps, WARPS) : WARPS;
     const int nw = c->cta_warps;
-    int cap = ((std::max(a.max_row, 32) + 31) / 32) * 32;
-    cap = std::min(cap, 1024);
+    const int cap = cap_s;
     c->cap = cap;
-    c->smem = (size_t)nw * cap * (tsz + sizeof(int));
+    c->smem = (size_t)nw * cap * (tsz + sizeof(int));      // batched kernels: uniform per-warp rows
     int per_sm = 0;
     if (f32) {
         CK(ensure_smem((const void *)k_refactor<float>, c->smem));
@@ -1972,6 +2247,61 @@ static kkt_status upload(kkt_ctx *c) {
     const int rows_cap = (n + nw - 1) / nw;
     int grid = c->opt.refactor_ctas > 0 ? std::min(c->opt.refactor_ctas, sms * per_sm) : sms * per_sm;
     c->grid = std::max(1, std::min(grid, rows_cap));
+    // k_refactor: every warp owns a block of shared memory with its row buffer
+    // (cap entries; big warps cap_big), then either the row's columns (no
+    // update maps: targets are found by binary search) or its staging ring
+    // (update maps: pivot rows fed ahead by cp.async, see Stage<T>).  Big warps
+    // only when the options ask for them.
+    {
+        const bool mapped = !a.upd_off.empty();
+        const bool staged = mapped;
+        const size_t ring = f32 ? (size_t)Stage<float>::RING : (size_t)Stage<double>::RING;
+        auto warp_bytes = [&](int capw) {
+            const size_t vb = ((size_t)capw * tsz + 15) & ~(size_t)15;
+            const size_t cb = ((size_t)capw * sizeof(int) + 15) & ~(size_t)15;
+            return vb + (staged ? ring : (mapped ? 0 : cb));
+        };
+        const size_t cta_max = 227 * 1024;
+        int nbig = 0, cap_big = cap;
+        if (!ord_long.empty() && nw >= 2 && c->opt.refactor_big_warps > 0) {
+            cap_big = ((a.max_row + 31) / 32) * 32;
+            while (cap_big > cap && warp_bytes(cap_big) + (size_t)(nw - 1) * warp_bytes(cap) > cta_max)
+                cap_big -= 32;
+            if (cap_big > cap) {
+                const long long each = (long long)warp_bytes(cap_big) - (long long)warp_bytes(cap);
+                const long long most = ((long long)cta_max - (long long)nw * (long long)warp_bytes(cap)) / each;
+                nbig = (int)std::max(1LL, std::min<long long>({(long long)c->opt.refactor_big_warps,
+                                                               (long long)nw / 2, most}));
+            } else {
+                cap_big = cap;
+            }
+        }
+        if (nbig == 0 && c->P.n_long > 0) {
+            // no big warps: every row in one queue
+            c->P.order_free = c->P.order_f;
+            c->P.n_free = n;
+            c->P.n_long = 0;
+        }
+        c->rc.nbig = nbig;
+        c->rc.cap_big = cap_big;
+        c->rc.smem_cols = mapped ? 0 : 1;
+        c->rc.staged = staged ? 1 : 0;
+        c->rc.warp_bytes_big = (int)warp_bytes(cap_big);
+        c->rc.warp_bytes_small = (int)warp_bytes(cap);
+        c->rsmem = (size_t)nbig * warp_bytes(cap_big) + (size_t)(nw - nbig) * warp_bytes(cap);
+        int per_sm_r = 0;
+        if (f32) {
+            CK(ensure_smem((const void *)k_refactor<float>, c->rsmem));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, k_refactor<float>, nw * 32, c->rsmem));
+        } else {
+            CK(ensure_smem((const void *)k_refactor<double>, c->rsmem));
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, k_refactor<double>, nw * 32, c->rsmem));
+        }
+        if (per_sm_r < 1) { g_last_error = "refactor kernel does not fit on an SM"; return KKT_ERR_CUDA; }
+        const int rg = c->opt.refactor_ctas > 0 ? std::min(c->opt.refactor_ctas, sms * per_sm_r)
+                                                : sms * per_sm_r;
+        c->rgrid = std::max(1, std::min(rg, rows_cap));
+    }
     // batched solves: 2 CTAs of cta_warps per SM; single-system solves: CTAs of
     // twice as many warps, one per SM (a CTA task gets the whole SM)
     c->bsolve_grid = std::max(1, std::min(sms * 2, rows_cap));
@@ -1981,17 +2311,20 @@ static kkt_status upload(kkt_ctx *c) {
     c->solve_grid = std::max(1, std::min(sgrid, (n + snw - 1) / snw));
     // rows longer than the shared-memory capacity work in global scratch
     if (a.max_row > cap) {
-        size_t per = (size_t)a.max_row;
-        CK(cudaMalloc(&c->d_scratch, per * tsz * c->grid * nw));
-        c->device_bytes += per * tsz * c->grid * nw;
+        const size_t per = (size_t)a.max_row, warps = (size_t)std::max(c->grid, c->rgrid) * nw;
+        CK(cudaMalloc(&c->d_scratch, per * tsz * warps));
+        c->device_bytes += per * tsz * warps;
         c->rc.scratch_stride = (int)per;
     }
     // update maps
     if (!a.upd_off.empty()) {
-        const size_t off_b = (size_t)nlu * sizeof(unsigned);
+        // the map starts on a 256-byte boundary and is readable 64 bytes past
+        // its end (16-byte copies of the staged refactorization)
+        const size_t off_b = ((size_t)nlu * sizeof(unsigned) + 255) & ~(size_t)255;
         const size_t map_b = a.upd_map.size() * sizeof(unsigned short);
-        CK(cudaMalloc(&c->d_maps, off_b + map_b + 16));
-        CK(cudaMemcpy(c->d_maps, a.upd_off.data(), off_b, cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&c->d_maps, off_b + map_b + 64));
+        CK(cudaMemset(c->d_maps, 0, off_b + map_b + 64));
+        CK(cudaMemcpy(c->d_maps, a.upd_off.data(), (size_t)nlu * sizeof(unsigned), cudaMemcpyHostToDevice));
         unsigned short *dm = (unsigned short *)((char *)c->d_maps + off_b);
         if (map_b) CK(cudaMemcpy(dm, a.upd_map.data(), map_b, cudaMemcpyHostToDevice));
         c->P.upd_off = (const unsigned *)c->d_maps;
@@ -2448,7 +2781,7 @@ template <typename T> static kkt_status launch_refactor(kkt_ctx *c, cudaStream_t
     // every entry starts as the not-ready marker; published entries overwrite it
     CK(cudaMemsetAsync(c->d_lu, 0xff, (size_t)c->nnz_lu * sizeof(T), s));
     CK(cudaMemsetAsync(c->d_rcp, 0xff, (size_t)c->an.n * sizeof(T), s));
-    k_refactor<T><<<c->grid, c->cta_warps * 32, c->smem, s>>>(c->P, c->rc, c->values, c->d_sp,
+    k_refactor<T><<<c->rgrid, c->cta_warps * 32, c->rsmem, s>>>(c->P, c->rc, c->values, c->d_sp,
                                                                (T *)c->d_lu, (T *)c->d_lut,
                                                                (T *)c->d_rcp, c->tau_rel);
     CK(cudaGetLastError());
@@ -3432,7 +3765,9 @@ kkt_status kkt_get_stats(const kkt_ctx *c, kkt_stats *o) {
     o->bytes_solve = (W + 4.0) * o->nnz_lu + 3.0 * 8.0 * n + 8.0 * n;
     o->bytes_spmv = 12.0 * o->nnz_a + 32.0 * n;
     o->device_bytes = c->device_bytes;
-    o->grid_ctas = c->grid;
+    o->grid_ctas = c->rgrid;
+    o->refactor_big_warps = c->rc.nbig;
+    o->refactor_big_cap = c->rc.cap_big;
     o->solve_ctas = c->solve_grid;
     o->warps_per_cta = c->cta_warps;
     o->last_refine_iters = c->last_iters;

@@ -44,7 +44,7 @@ class KKTSolver:
                  perm=None, refine_mode="classic", tol=1e-14, max_refine=20,
                  pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
                  solve_ctas=0, update_map_budget=0, trace=False, max_batch=1, unpublished_row=-1,
-                 poll_ns_max=0, device=0):
+                 poll_ns_max=0, refactor_big_warps=0, device=0):
         self._lib = _capi.load()
         self.n = int(n)
         self._rp = _i32(indptr)
@@ -72,6 +72,7 @@ class KKTSolver:
         opt.max_batch = int(max_batch)
         opt.unpublished_row = int(unpublished_row)
         opt.poll_ns_max = int(poll_ns_max)
+        opt.refactor_big_warps = int(refactor_big_warps)
         self.device = None if device is None else torch.device("cuda", int(device)) if not isinstance(
             device, torch.device) else device
         opt.device = -1 if self.device is None else (self.device.index or 0)
