@@ -1,19 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the fixed-pattern KKT refactorization path on GB300.
 
-Workload (default): the 2,000-bus sequence, plain FP64 plus adjoint (KKT
-dimension 14,000, 140,400 stored entries, 30 value sets whose D_x, D_s widen
-to [1e-8, 1e8]).  One step is one KKT system of the sequence through the
-whole path: refactorization, solve, iterative refinement to scaled residual
-1e-14, transposed solve with its refinement, and the adjoint gather (the
-backward of x = A^-1 b).  All value sets, right-hand sides and upstream
-gradients are resident in HBM before the timed region; L2 is flushed between
-timed steps (a 256 MiB write, outside the per-step events).
+Workload (default): the 70,000-bus late-IPM system with FP32 factors and FP64
+refinement (KKT dimension 490,000, 4,914,000 stored entries, 4 value sets with
+D_x, D_s log-uniform in [1e-8, 1e8]), the largest single-GPU configuration.
+``--workload 2000bus_fp64_adjoint`` runs the 2,000-bus plain FP64 sequence
+(n = 14,000, 30 value sets).  One step is one KKT system through the whole
+path: refactorization, solve, iterative refinement to scaled residual 1e-14,
+transposed solve with its refinement, and the adjoint gather (the backward of
+x = A^-1 b).  All value sets, right-hand sides and upstream gradients are
+resident in HBM before the timed region; L2 is flushed between timed steps
+(a 256 MiB write, outside the per-step events).
 
 Metric: microseconds per KKT system (lower is better) and HBM GB/s.  The
 ``e2e`` figure runs the same step from pinned host buffers through the C
 interface, copies included.  ``--impl reference`` times the CPU oracle on the
-host cores on the same workload (a bounded sample per step).
+host cores on the same workload (a bounded sample: whole systems until a CPU
+time budget is spent).
 
 Multi-GPU (torchrun): every rank runs its own replica of the sequence on its
 own GPU (independent systems, no collective on the data path); the reported
@@ -40,12 +43,16 @@ import numpy as np
 METRIC = "refactor+solve µs per KKT system and HBM GB/s on 1 GB300; batched/FP32 vs plain"
 UNIT = "us/system"
 WORKLOADS = {
-    "2000bus_fp64_adjoint": dict(cfg=1, fp32=False),
-    "200bus_fp64": dict(cfg=0, fp32=False),
+    "70000bus_fp32_refined": dict(cfg=3, fp32=True, refine="auto"),
+    "2000bus_fp64_adjoint": dict(cfg=1, fp32=False, refine="classic"),
+    "200bus_fp64": dict(cfg=0, fp32=False, refine="classic"),
 }
+DEFAULT_WORKLOAD = "70000bus_fp32_refined"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (non-tensor and tensor), nominal
 HBM_FALLBACK_GBS = 6800.0
+# nominal non-tensor FMA rates of GB300 (152 SMs at 2.07 GHz): FP32 128 lanes
+# per SM, FP64 2 lanes per SM (x 2 flops per FMA); the bench measures its own
+FMA_NOMINAL_TFLOPS = {"f32": 152 * 128 * 2 * 2.07e9 / 1e12, "f64": 152 * 2 * 2 * 2.07e9 / 1e12}
 
 
 def _dist_env():
@@ -174,40 +181,107 @@ def committed_traffic(kernel: str, workload: str):
 
 
 # ----------------------------------------------------------------- oracle leg
-def oracle_sample(seq, step_ids, budget_s: float):
+def oracle_sample(seq, step_ids, budget_s: float, refine_mode: str = "auto", keep_first=False, perm=None):
     """Time the oracle (as it stands, single-threaded) on whole steps of the
-    workload until ``budget_s`` seconds of CPU work are spent; returns
-    (us per system, systems timed)."""
+    workload -- factorization, solve, refinement, transposed solve with its
+    refinement, adjoint -- until ``budget_s`` seconds of CPU work are spent.
+    The ordering is computed once outside the timing (the symbolic phase, as
+    for the GPU).  Returns (us per system, systems timed, results of the first
+    step: x and lambda, refined to 1e-14, or None)."""
     import oracle
-    perm = oracle.min_degree(seq.n, seq.indptr, seq.indices)   # ordering: outside, like analyze
-    rng = np.random.default_rng(7)
-    done, t_total = 0, 0.0
+    if perm is None:
+        perm = oracle.min_degree(seq.n, seq.indptr, seq.indices)
+    done, t_total, first = 0, 0.0, None
     for k in step_ids:
         v, b = seq.values(k), seq.rhs(k)
-        g = rng.standard_normal(seq.n)
+        g = np.random.default_rng(1234 + k).standard_normal(seq.n)
         t0 = time.perf_counter()
         o = oracle.Oracle(seq.n, seq.indptr, seq.indices, v, perm)
-        x = o.solve(b)
-        x, *_ = o.refine(b, x0=x)
+        x, *_ = o.refine(b, x0=o.solve(b), mode=refine_mode)
+        # transposed solve, refined classically with the same factors
+        At = seq.csr(k).T.tocsr()
+        lam = o.solve_t(g)
+        for _ in range(20):
+            if oracle.omega(seq.n, At.indptr, At.indices, At.data, g, lam) <= 1e-14:
+                break
+            lam = lam + o.solve_t(oracle.residual(seq.n, At.indptr, At.indices, At.data, g, lam))
         o.adjoint(x, g)
         t_total += time.perf_counter() - t0
+        if keep_first and first is None:
+            first = {"k": k, "x": x, "lam": lam}
         done += 1
         if t_total >= budget_s:
             break
-    return t_total * 1e6 / max(done, 1), done
+    return t_total * 1e6 / max(done, 1), done, first
+
+
+def _oracle_omega_pool(args_list):
+    """Worker of the all-cores oracle timing (one system per task, spawn pool)."""
+    import oracle
+    n, rp, ci, v, b, perm = args_list
+    t0 = time.perf_counter()
+    o = oracle.Oracle(n, rp, ci, v, perm)
+    x, *_ = o.refine(b, x0=o.solve(b))
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(systems, budget_s: float):
+    """Independent systems (n, rp, ci, values, b) through the oracle (factor,
+    solve, refine) on every host core with a spawn process pool, until about
+    ``budget_s`` of wall time: (us per system of wall time, systems, cores)."""
+    import multiprocessing as mp
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    perms = {}
+    tasks = []
+    for (n, rp, ci, v, b) in systems:
+        key = (n, len(ci), int(rp[-1]), int(ci[:64].sum()))
+        if key not in perms:
+            perms[key] = oracle.min_degree(n, rp, ci)
+        tasks.append((n, rp, ci, v, b, perms[key]))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    done = 0
+    with ctx.Pool(cores) as pool:
+        for _ in pool.imap_unordered(_oracle_omega_pool, tasks):
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                pool.terminate()
+                break
+    wall = time.perf_counter() - t0
+    return wall * 1e6 / max(done, 1), done, cores
+
+
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args, ws, rank):
-    """--impl reference: the CPU oracle on the host cores, same metric."""
+    """--impl reference: the CPU oracle on the host cores, same metric and
+    workload.  A step is one whole system; warm-up steps and timed steps each
+    stop at a CPU-time budget (one system at least), so the run ends within a
+    few minutes also on the 490,000-row workload (about 20-40 s per system)."""
     if rank != 0:
         return 0
     from kktgen import config_sequence
     wl = WORKLOADS[args.workload]
     seq = config_sequence(wl["cfg"])
+    import oracle
     ids = [k % seq.steps for k in range(args.warmup + args.steps)]
-    oracle_sample(seq, ids[: args.warmup], 1e9)
-    us, done = oracle_sample(seq, ids[args.warmup:], 1e9)
+    perm = oracle.min_degree(seq.n, seq.indptr, seq.indices)       # symbolic: outside the timing
+    oracle_sample(seq, ids[: args.warmup], min(args.cpu_budget, 10.0), wl["refine"], perm=perm)
+    us, done, _ = oracle_sample(seq, ids[args.warmup:], args.ref_budget, wl["refine"], perm=perm)
     cores = 1
+    sample = (f"{done} of the {args.steps} requested steps (whole systems: refactor, solve, refine, "
+              f"transposed solve + refine, adjoint) of the {args.workload} sequence, single-threaded, "
+              f"bounded at {args.ref_budget:.0f} s of CPU time; warm-up bounded at 10 s")
     line = {
         "impl": "reference", "metric": METRIC, "value": us, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": us / 1e3,
@@ -215,13 +289,29 @@ def run_reference(args, ws, rank):
         "data": "synthetic",
         "config": {"workload": args.workload, "n": seq.n, "nnz": seq.nnz, "value_sets": seq.steps,
                    "l2": "host cores (no GPU cache)", "parallelism": "one host core"},
-        "cpu_baseline": {"value": us, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{done} whole steps (refactor, solve, refine, transposed solve, adjoint) "
-                                   f"of the {args.workload} sequence, single-threaded"},
+        "cpu_baseline": {"value": us, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model()},
         "e2e": {"value": us, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def probe_fma(dev_index):
+    """Measured FMA rates (TFLOP/s) of this GPU from the library's probe."""
+    import ctypes as C
+    from paper_2306_14337_gb300 import _capi
+    L = _capi.load()
+    out = {}
+    for key, fp64 in (("f32", 0), ("f64", 1)):
+        v = C.c_double(0.0)
+        if L.kkt_probe_fma_tflops(int(dev_index), fp64, C.byref(v)) == 0:
+            out[key] = v.value
+    return out
+
+
+def _relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -239,12 +329,12 @@ def run_native(args, ws, rank, local):
     wl = WORKLOADS[args.workload]
     seq = config_sequence(wl["cfg"])
     n, nnz, K = seq.n, seq.nnz, seq.steps
-    S = KKTSolver(n, seq.indptr, seq.indices, fp32=wl["fp32"], device=local)
-    st0 = S.stats()
+    S = KKTSolver(n, seq.indptr, seq.indices, fp32=wl["fp32"], refine_mode=wl["refine"], device=local)
+    dname = "f32" if wl["fp32"] else "f64"
     rng = np.random.default_rng(1234 + rank)
     vals = [torch.tensor(seq.values(k), device=dev) for k in range(K)]
     bs = [torch.tensor(seq.rhs(k), device=dev) for k in range(K)]
-    gs = [torch.tensor(rng.standard_normal(n), device=dev) for k in range(K)]
+    gs = [torch.tensor(np.random.default_rng(1234 + k).standard_normal(n), device=dev) for k in range(K)]
     x = torch.empty(n, dtype=torch.float64, device=dev)
     lam = torch.empty_like(x)
     dA = torch.empty(nnz, dtype=torch.float64, device=dev)
@@ -300,7 +390,7 @@ def run_native(args, ws, rank, local):
             raise SystemExit(f"refinement did not converge at step {k}: {r1} {r2}")
     torch.cuda.synchronize()
     barrier(ws)
-    launches = S.stats()["kernel_launches"] - launches0 - 0
+    launches = S.stats()["kernel_launches"] - launches0
     total_s = sum(step_ms) / 1e3
     total_s = reduce_max(total_s, ws, dev)
     clk = clocks.stop()
@@ -339,69 +429,87 @@ def run_native(args, ws, rank, local):
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_s = reduce_max(sum(e2e_ms) / 1e3, ws, dev)
 
-    # CPU baseline (rank 0, N = 1 only): the oracle on a bounded sample
-    cpu = None
+    # the GPU's results for value set 0, kept for the FP64-oracle comparison
+    step(0)
+    torch.cuda.synchronize()
+    x0, lam0 = x.cpu().numpy().copy(), lam.cpu().numpy().copy()
+
+    # CPU baseline (rank 0, N = 1 only): the oracle on a bounded sample, whose
+    # first system (value set 0) is also the FP64 reference of the results
+    cpu, oracle_err = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        us_cpu, done = oracle_sample(seq, list(range(K)), args.cpu_budget)
-        cpu = {"value": us_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{done} whole steps of the {args.workload} sequence, single-threaded, "
-                         f"ordering computed once outside the timing"}
+        import oracle
+        us_cpu, done, first = oracle_sample(seq, list(range(K)), args.cpu_budget, wl["refine"], keep_first=True)
+        cpu = {"value": us_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu_model(),
+               "sample": f"{done} whole system(s) (refactor, solve, refine, transposed solve + refine, "
+                         f"adjoint) of the {args.workload} sequence, single-threaded, ordering computed "
+                         f"once outside the timing, bounded at {args.cpu_budget:.0f} s of CPU time"}
+        At = seq.csr(0).T.tocsr()
+        oracle_err = {
+            "value_set": 0,
+            "x_rel_err_inf": _relerr(x0, first["x"]), "lambda_rel_err_inf": _relerr(lam0, first["lam"]),
+            "omega_x_by_oracle": oracle.omega(n, seq.indptr, seq.indices, seq.values(0), seq.rhs(0), x0),
+            "omega_lambda_by_oracle": oracle.omega(n, At.indptr, At.indices, At.data,
+                                                   np.random.default_rng(1234).standard_normal(n), lam0),
+            "note": "both solutions are refined to omega <= 1e-14; their difference is bounded by "
+                    "cond(A) * 1e-14, and cond(A) reaches ~1e10 with D in [1e-8, 1e8]"}
 
     variants = {}
     if rank == 0 and not args.no_variants:
-        variants = run_variants(dev)
+        variants = run_variants(dev, with_oracle=not args.no_cpu_baseline, budget=args.cpu_budget)
 
     if rank != 0:
         return 0
     us = whole_job_us_per_system(total_s, args.steps, ws)
     ph_ms = {k: statistics.mean(v) for k, v in phase.items()}
-    # dominant phase and its roofline
     st = S.stats()
     peak_hbm, peak_kind = load_peaks()
-    flops = st["flops_refactor"]
-    dom = max(ph_ms, key=ph_ms.get)
-    fp64_peak_tflops = FP64_NOMINAL_TFLOPS
-    if dom == "refactor":
-        # FP64 FMA work dominates bytes by ~15x on this workload: ALU-bound roofline
-        achieved = flops / (ph_ms["refactor"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_refactor<double> (+k_scale, k_amax)",
-                "achieved": achieved, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak_tflops,
-                "peak_source": "nominal GB300 FP64 rate (a DFMA probe measured 1.2 TFLOP/s)",
-                "algorithmic_flops_per_launch": flops,
-                "traffic": committed_traffic("k_refactor_f64", args.workload)}
-    else:
-        # triangular solves: bytes of the factor read once per solve
-        nsolves = {"solve": 1, "refine": max(1, statistics.mean(i[0] for i in iters)),
-                   "transpose": 1 + statistics.mean(i[1] for i in iters)}.get(dom, 1)
-        by = st["bytes_solve"] * nsolves
-        achieved = by / (ph_ms[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": f"{dom} (k_trisolve)", "achieved": achieved,
-                "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm,
-                "peak_source": peak_kind, "algorithmic_bytes_per_launch": by,
-                "traffic": committed_traffic("k_trisolve_f64", args.workload)}
-    ref_bytes = st["bytes_refactor"]
+    fma = probe_fma(local)
+    alu_peak = fma.get(dname, FMA_NOMINAL_TFLOPS[dname])
+    # dominant kernel: the refactorization (k_refactor; k_scale, k_amax and
+    # k_pack_tiles share its events and are a few percent of it)
+    t_ref = ph_ms["refactor"] * 1e-3
+    by_ref = st["bytes_refactor"]
+    achieved = by_ref / t_ref / 1e9
+    roof = {"bound": "hbm", "kernel": f"k_refactor<{'float' if wl['fp32'] else 'double'}> "
+                                      f"(+k_scale, k_amax, k_pack_tiles in the same events)",
+            "achieved": achieved, "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": by_ref,
+            "traffic": committed_traffic(f"k_refactor_{dname}", args.workload),
+            "alu_achieved_tflops": st["flops_refactor"] / t_ref / 1e12, "alu_peak_tflops": alu_peak,
+            "alu_frac": st["flops_refactor"] / t_ref / 1e12 / alu_peak,
+            "alu_peak_source": ("measured by kkt_probe_fma_tflops on this GPU" if dname in fma
+                                else "nominal")}
+    rs_s = (ph_ms["refactor"] + ph_ms["solve"]) * 1e-3
+    rs_bytes = st["bytes_refactor"] + st["bytes_solve"]
     line = {
         "metric": METRIC, "value": us, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if wl["fp32"] else "f64", "data": "synthetic",
+        "dtype": dname, "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "nnz": nnz, "nnz_lu": st["nnz_lu"],
                    "levels": st["n_levels"], "value_sets": K,
+                   "factors": "FP32, FP64 residual/refinement/pivot test" if wl["fp32"] else "FP64",
+                   "refine": wl["refine"],
                    "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                    "parallelism": f"replicas x{ws}"},
         "breakdown_ms": ph_ms,
-        "refactor_hbm_gbs": ref_bytes / (ph_ms["refactor"] * 1e-3) / 1e9,
+        "refactor_solve_us": rs_s * 1e6,
+        "refactor_solve_hbm_gbs": rs_bytes / rs_s / 1e9,
+        "refactor_solve_hbm_frac": rs_bytes / rs_s / 1e9 / peak_hbm,
         "refine_iters": {"solve": statistics.mean(i[0] for i in iters),
                          "transpose": statistics.mean(i[1] for i in iters)},
         "omega_max": max(omegas), "status": int(st_code), "perturbed_pivots": npert,
         "roofline": roof,
+        "fma_probe_tflops": fma,
         # Why the fraction is low: the refactorization is a chain of dependent
         # rows, one hand-off per level of the elimination DAG.
         "critical_path": {"refactor_levels": st["n_levels"],
                           "refactor_us_per_level": ph_ms["refactor"] * 1e3 / st["n_levels"],
                           "solve_levels": {"forward": st["n_levels"], "backward": st["n_levels_u"]},
                           "solve_tasks": st["n_tasks"], "longest_task_rows": st["max_task"]},
+        "oracle_error": oracle_err,
         "cpu_baseline": cpu,
         "e2e": {"value": whole_job_us_per_system(e2e_s, args.steps, ws), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (nnz + 2 * n), "d2h_bytes_per_step": 8 * (nnz + 2 * n)},
@@ -431,7 +539,7 @@ def _time_ms(fn, reps=3):
     return statistics.median(out)
 
 
-def run_uneven(dev):
+def run_uneven(dev, with_oracle=True, budget=15.0):
     """48 systems with different patterns (16 x 500, 16 x 2,000, 12 x 5,000,
     4 x 20,000 buses): FP32 factors, one work queue and one CUDA graph per
     phase sequence (refactor, solve, 8 classic refinement steps), launch shape
@@ -486,54 +594,105 @@ def run_uneven(dev):
             S.refine(bs[k], xp[k], 1e-14, 20)
             S.solve_transpose(gs[k], out=lams[k])
     tp = _time_ms(run_plain, reps=2)
-    return {"us_per_system": tq * 1e3 / len(seqs), "plain_fp64_us_per_system": tp * 1e3 / len(seqs),
-            "speedup_vs_plain": tp / tq, "systems": len(seqs), "omega_max": worst,
-            "finished_outside_graph": state.get("late"), "launch_shape": list(best),
-            "tuning_ms": {f"{w}x{c}": t * 1e3 for (w, c), t in (table or {}).items()}}
+    out = {"us_per_system": tq * 1e3 / len(seqs), "plain_fp64_us_per_system": tp * 1e3 / len(seqs),
+           "speedup_vs_plain": tp / tq, "systems": len(seqs), "omega_max": worst,
+           "finished_outside_graph": state.get("late"), "launch_shape": list(best),
+           "tuning_ms": {f"{w}x{c}": t * 1e3 for (w, c), t in (table or {}).items()}}
+    if with_oracle:
+        import oracle
+        # FP64-oracle error of the solution of one system of each size
+        errs = {}
+        run()
+        for k in (0, 16, 32, 44):
+            q = seqs[k]
+            sols[k].refine(bs[k], xs[k], 1e-14, 20)
+            o = oracle.Oracle(q.n, q.indptr, q.indices, q.values(0), oracle.min_degree(q.n, q.indptr, q.indices))
+            xo, *_ = o.refine(q.rhs(0))
+            xh = xs[k].cpu().numpy()
+            errs[f"n{q.n}"] = {"x_rel_err_inf": _relerr(xh, xo),
+                               "omega_x_by_oracle": oracle.omega(q.n, q.indptr, q.indices, q.values(0),
+                                                                 q.rhs(0), xh)}
+        out["oracle_error"] = errs
+        us_all, done, cores = oracle_all_cores(
+            [(q.n, q.indptr, q.indices, q.values(0), q.rhs(0)) for q in seqs], budget)
+        out["cpu_baseline_all_cores"] = {
+            "value": us_all, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{done} of the 48 systems (factor, solve, refine), one per process, spawn pool, "
+                      f"wall time per system"}
+    return out
 
 
-def run_variants(dev):
+def run_variants(dev, with_oracle=True, budget=15.0):
     """The batched and FP32 forms against the plain FP64 path on the same GPU,
     all refined to scaled residual <= 1e-14 (per system, microseconds):
       batched: 64 scenario systems of the 10,000-bus grid (loads scaled by
-               U(0.8, 1.2)), one batched refactor + solve + refine;
-      fp32:    the 70,000-bus late-IPM system, FP32 factors + FP64 refinement."""
+               U(0.8, 1.2)), one batched refactor + solve + refine per IPM step,
+               5 steps;
+      fp32:    the 70,000-bus late-IPM system, FP32 factors + FP64 refinement,
+               against plain FP64 factors;
+      uneven:  the 48 systems of different patterns in one work queue;
+      2000bus: the 2,000-bus plain FP64 step of the adjoint workload.
+    With the oracle: the FP64-oracle error of sampled results and the oracle
+    timed on all host cores for the batched and uneven forms."""
     import torch
     from kktgen import config_sequence
     from paper_2306_14337_gb300 import KKTSolver
     res = {}
-    # batched, 10,000-bus x 64
+    # batched, 10,000-bus x 64, all 5 IPM steps of the sequence
     s = config_sequence(2)
-    k, B = 2, 64
-    vals = torch.tensor(np.stack([s.values(k, sc) for sc in range(1, B + 1)], axis=1), device=dev)
-    bs = torch.tensor(np.stack([s.csr(k, sc) @ s.x_true(k, sc) for sc in range(1, B + 1)], axis=1),
-                      device=dev)
+    B = 64
+    steps = list(range(s.steps))
+    vals = [torch.tensor(np.stack([s.values(k, sc) for sc in range(1, B + 1)], axis=1), device=dev)
+            for k in steps]
+    bs = [torch.tensor(np.stack([s.csr(k, sc) @ s.x_true(k, sc) for sc in range(1, B + 1)], axis=1),
+                       device=dev) for k in steps]
     Sb = KKTSolver(s.n, s.indptr, s.indices, max_batch=B)
-    xb = torch.empty_like(bs)
-    info = {}
+    xb = torch.empty_like(bs[0])
+    info = {"omega": 0.0, "iters": []}
 
     def batched():
-        Sb.batch_refactor(vals)
-        Sb.batch_solve(bs, out=xb)
-        info["r"] = Sb.batch_refine(bs, xb, 1e-14, 40)
+        for k in steps:
+            Sb.batch_refactor(vals[k])
+            Sb.batch_solve(bs[k], out=xb)
+            r = Sb.batch_refine(bs[k], xb, 1e-14, 40)
+            info["omega"] = max(info["omega"], float(np.max(r["omega"])))
+            info["iters"].append(r["iters"])
     tb = _time_ms(batched)
     S1 = KKTSolver(s.n, s.indptr, s.indices)
-    v1 = vals[:, 0].contiguous()
-    b1 = bs[:, 0].contiguous()
-    x1 = torch.empty_like(b1)
+    x1 = torch.empty(s.n, dtype=torch.float64, device=dev)
+    v1 = [vals[k][:, 0].contiguous() for k in steps]
+    b1 = [bs[k][:, 0].contiguous() for k in steps]
     info1 = {}
 
     def plain():
-        S1.refactor(v1)
-        S1.solve(b1, out=x1)
-        info1["r"] = S1.refine(b1, x1, 1e-14, 20)
+        for k in steps:
+            S1.refactor(v1[k])
+            S1.solve(b1[k], out=x1)
+            info1["r"] = S1.refine(b1[k], x1, 1e-14, 20)
     tp = _time_ms(plain)
-    res["batched_10000bus_x64_fp64"] = {
-        "us_per_system": tb * 1e3 / B, "plain_fp64_us_per_system": tp * 1e3,
-        "speedup_vs_plain": tp * B / tb, "omega_max": float(np.max(info["r"]["omega"])),
-        "refine_iters": info["r"]["iters"], "n": s.n, "batch": B}
+    nsys = B * len(steps)
+    bat = {"us_per_system": tb * 1e3 / nsys, "plain_fp64_us_per_system": tp * 1e3 / len(steps),
+           "speedup_vs_plain": (tp / len(steps)) / (tb / nsys), "omega_max": info["omega"],
+           "refine_iters": info["iters"][-len(steps):], "n": s.n, "batch": B, "ipm_steps": len(steps)}
+    if with_oracle:
+        import oracle
+        k = steps[-1]
+        xh = xb.cpu().numpy()
+        v0, b0 = vals[k][:, 0].cpu().numpy(), bs[k][:, 0].cpu().numpy()
+        o = oracle.Oracle(s.n, s.indptr, s.indices, v0, oracle.min_degree(s.n, s.indptr, s.indices))
+        xo, *_ = o.refine(b0)
+        bat["oracle_error"] = {"scenario": 0, "ipm_step": k, "x_rel_err_inf": _relerr(xh[:, 0], xo),
+                               "omega_x_by_oracle": oracle.omega(s.n, s.indptr, s.indices, v0, b0, xh[:, 0])}
+        us_all, done, cores = oracle_all_cores(
+            [(s.n, s.indptr, s.indices, vals[k][:, j].cpu().numpy(), bs[k][:, j].cpu().numpy())
+             for j in range(B)], budget)
+        bat["cpu_baseline_all_cores"] = {
+            "value": us_all, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{done} of the 64 scenario systems of the last IPM step (factor, solve, refine), "
+                      f"one per process, spawn pool, wall time per system"}
+    res["batched_10000bus_x64_fp64"] = bat
     del Sb, S1, vals, bs
-    # FP32 factors + FP64 refinement, 70,000-bus
+    # FP32 factors + FP64 refinement against plain FP64, 70,000-bus
     s = config_sequence(3)
     v = torch.tensor(s.values(0), device=dev)
     b = torch.tensor(s.rhs(0), device=dev)
@@ -552,23 +711,42 @@ def run_variants(dev):
         del S
     t32, r32, st = out["fp32"]
     t64, r64, _ = out["fp64"]
-    res["uneven_48_fp32_queue"] = run_uneven(dev)
     res["fp32_refined_70000bus"] = {
         "us_per_system": t32 * 1e3, "plain_fp64_us_per_system": t64 * 1e3,
         "speedup_vs_plain": t64 / t32, "omega": r32["omega"], "refine_iters": r32["iters"],
-        "fp64_omega": r64["omega"], "n": s.n, "nnz_lu": st["nnz_lu"], "levels": st["n_levels"],
-        "hbm_gbs_refactor_solve_fp32": (st["bytes_refactor"] + st["bytes_solve"]) / (t32 * 1e-3) / 1e9}
+        "fp64_omega": r64["omega"], "n": s.n, "nnz_lu": st["nnz_lu"], "levels": st["n_levels"]}
+    del v, b
+    res["uneven_48_fp32_queue"] = run_uneven(dev, with_oracle, budget)
+    # the 2,000-bus FP64 step (refactor, solve, refine, transposed solve + refine, adjoint)
+    s = config_sequence(1)
+    S = KKTSolver(s.n, s.indptr, s.indices)
+    v = torch.tensor(s.values(29), device=dev)
+    b = torch.tensor(s.rhs(29), device=dev)
+    g = torch.tensor(np.random.default_rng(5).standard_normal(s.n), device=dev)
+    x, lam = torch.empty_like(b), torch.empty_like(b)
+    dA = torch.empty(s.nnz, dtype=torch.float64, device=dev)
+
+    def step2k():
+        S.refactor(v)
+        S.solve(b, out=x)
+        S.refine(b, x, 1e-14, 20)
+        S.solve_transpose(g, out=lam)
+        S.refine_transpose(g, lam, 1e-14, 20)
+        S.adjoint_gather(lam, x, out=dA)
+    res["fp64_adjoint_2000bus"] = {"us_per_system": _time_ms(step2k, reps=10) * 1e3, "n": s.n}
     return res
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="2000bus_fp64_adjoint")
-    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work per CPU leg")
+    ap.add_argument("--ref-budget", type=float, default=60.0,
+                    help="--impl reference: seconds of oracle work over the timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the batched and FP32 comparisons (about a minute)")

@@ -53,7 +53,7 @@ CONFIGS = {
     2: dict(name="batched FP64, 10,000-bus x 64 scenarios", nb=10000, nl=13000, ng=2000,
             steps=5, W=8.0, widen=True, scenarios=64),
     3: dict(name="FP32 factors + FP64 refinement, 70,000-bus late-IPM", nb=70000, nl=91000,
-            ng=14000, steps=1, W=8.0, widen=False, scenarios=1),
+            ng=14000, steps=4, W=8.0, widen=False, scenarios=1),
 }
 # Uneven batch: (buses, lines, generators, count)
 UNEVEN = [(500, 650, 100, 16), (2000, 2600, 400, 16), (5000, 6500, 1000, 12),

@@ -18,19 +18,31 @@ def _run(*args):
 
 
 def test_reference_arm_prints_one_contract_line():
-    out = _run("--impl", "reference", "--steps", "1", "--warmup", "3")
+    out = _run("--impl", "reference", "--steps", "2", "--warmup", "3", "--workload", "2000bus_fp64_adjoint")
     assert out.returncode == 0, out.stderr
     lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "us/system" and d["higher_is_better"] is False
-    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["config"]["workload"] == "2000bus_fp64_adjoint" and d["data"] == "synthetic"
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert cb["sample"].startswith("2 of the 2 requested steps") and "bounded" in cb["sample"]
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_default_workload_is_the_largest_single_gpu_configuration():
+    sys.path.insert(0, ROOT)
+    import bench
+    from kktgen import config_sequence
+    assert bench.DEFAULT_WORKLOAD == "70000bus_fp32_refined"
+    cfg = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
+    assert cfg["fp32"] and cfg["refine"] == "auto"
+    sizes = [config_sequence(c).n for c in (0, 1, 3)]
+    assert config_sequence(cfg["cfg"]).n == max(sizes) == 490_000
 
 
 def test_timing_rules_are_enforced():
