@@ -715,6 +715,28 @@ def run_variants(dev, with_oracle=True, budget=15.0):
         "us_per_system": t32 * 1e3, "plain_fp64_us_per_system": t64 * 1e3,
         "speedup_vs_plain": t64 / t32, "omega": r32["omega"], "refine_iters": r32["iters"],
         "fp64_omega": r64["omega"], "n": s.n, "nnz_lu": st["nnz_lu"], "levels": st["n_levels"]}
+    # symmetric values: LDL^T refactorization (same storage and solves) with inertia
+    ld = {}
+    for fp32 in (False, True):
+        S = KKTSolver(s.n, s.indptr, s.indices, fp32=fp32, refine_mode="auto", symmetric=True)
+        x = torch.empty_like(b)
+        inf = {}
+
+        def run_ld():
+            S.refactor(v)
+            S.solve(b, out=x)
+            inf["r"] = S.refine(b, x, 1e-14, 20)
+        t = _time_ms(run_ld, reps=2)
+        tr = _time_ms(lambda: S.refactor(v), reps=3)
+        pos, neg, pert = S.inertia()
+        ld["fp32" if fp32 else "fp64"] = {
+            "us_per_system": t * 1e3, "refactor_us": tr * 1e3, "omega": inf["r"]["omega"],
+            "refine_iters": inf["r"]["iters"], "inertia": {"positive": pos, "negative": neg,
+                                                           "perturbed": pert}}
+        del S
+    ld["speedup_vs_plain_fp64_lu"] = t64 / (ld["fp64"]["us_per_system"] / 1e3)
+    ld["n_x"] = 2 * s.grid.nb + 2 * s.grid.ng
+    res["ldlt_symmetric_70000bus"] = ld
     del v, b
     res["uneven_48_fp32_queue"] = run_uneven(dev, with_oracle, budget)
     # the 2,000-bus FP64 step (refactor, solve, refine, transposed solve + refine, adjoint)

@@ -58,7 +58,7 @@ typedef enum {
 } kkt_status;
 
 enum { KKT_ORDER_AMD = 0, KKT_ORDER_NATURAL = 1, KKT_ORDER_USER = 2 };
-enum { KKT_REFINE_CLASSIC = 0, KKT_REFINE_FGMRES = 1, KKT_REFINE_AUTO = 2 };
+enum { KKT_REFINE_CLASSIC = 0, KKT_REFINE_FGMRES = 1, KKT_REFINE_AUTO = 2, KKT_REFINE_FGMRES_JACOBI = 3 };
 
 typedef struct {
     int factor_fp32;        /* 0: factors and triangular solves in FP64;
@@ -72,7 +72,10 @@ typedef struct {
     int refine_mode;        /* KKT_REFINE_*: classic (Sec. 5.1 x += K^-1 (r - K x)),
                                FGMRES with the LU solve as right preconditioner and
                                CGS2 (Sec. 5.1), or classic switching to FGMRES when an
-                               iteration fails to halve the scaled residual */
+                               iteration fails to halve the scaled residual, or
+                               FGMRES whose preconditioner replaces the two
+                               triangular solves by jacobi_sweeps Jacobi sweeps each
+                               (Sec. 6: iterative approximate triangular solves) */
     int fgmres_restart;     /* Krylov basis size (default 20) */
     int max_refine;         /* default limit on solves in kkt_refine (20, Sec. 5.3) */
     double tol;             /* default scaled-residual target (1e-14, Sec. 5.3) */
@@ -103,6 +106,17 @@ typedef struct {
                                entries (k > 0: k, at most half the CTA, as far as
                                shared memory allows; 0 = none: such rows work in
                                global scratch, the faster choice where measured) */
+    int symmetric;          /* 1: the values are symmetric (A = A^T, as the KKT matrices
+                               of Eq. 4); the refactorization then computes A' = L D L^T
+                               (Sec. 3 inertia, Sec. 5.3 MA57's form): row i's multipliers
+                               l(i,d) = u(d,i)/u(d,d) come from rows below it, only its
+                               U part is reduced (half the flops of LU), the factors are
+                               stored as for LU, and kkt_inertia reports the pivot signs.
+                               Only A's upper triangle is read.  Needs the update maps
+                               (else the LU refactorization runs, same factors in exact
+                               arithmetic).  Batched and queued calls use LU. */
+    int jacobi_sweeps;      /* sweeps per triangular factor of KKT_REFINE_FGMRES_JACOBI
+                               (default 8) */
 } kkt_options;
 
 typedef struct {
@@ -184,6 +198,20 @@ kkt_status kkt_refactor(kkt_ctx *ctx, const double *values_dev, kkt_stream strea
  * b_dev, x_dev: n float64; they may not alias. */
 kkt_status kkt_solve(kkt_ctx *ctx, const double *b_dev, double *x_dev, kkt_stream stream);
 
+/*
+ * Approximate solve with the current factors by Jacobi sweeps instead of
+ * substitution (Sec. 6: iterative approximation of the triangular solves;
+ * Anzt, Chow and Dongarra 2015).  With L = I + L_s and U = D + U_s:
+ *   w_0 = c, w_{k+1} = c - L_s w_k;  z_0 = D^-1 w, z_{k+1} = D^-1 (w - U_s z_k),
+ * `sweeps` sweeps each, c = S P b and x = S P^T z (transpose = 1: the same on
+ * A'^T = U^T L^T).  Every sweep is one parallel sparse product with no
+ * dependency chain; the result equals the exact solve once sweeps reaches
+ * the number of levels minus one, and is an approximation (a preconditioner
+ * for FGMRES) below that.  b_dev, x_dev: n float64, not aliased.
+ */
+kkt_status kkt_solve_jacobi(kkt_ctx *ctx, const double *b_dev, double *x_dev, int sweeps, int transpose,
+                            kkt_stream stream);
+
 /* lam = A^-T g with the same factors (A'^T = U^T L^T).  g_dev, lam_dev: n float64. */
 kkt_status kkt_solve_transpose(kkt_ctx *ctx, const double *g_dev, double *lam_dev,
                                kkt_stream stream);
@@ -217,6 +245,18 @@ kkt_status kkt_adjoint_gather(kkt_ctx *ctx, const double *lam_dev, const double 
  * KKT_ERR_INTERNAL, KKT_ERR_TIMEOUT, KKT_ERR_NONFINITE, KKT_WARN_PERTURBED or KKT_OK;
  * *n_perturbed (may be NULL) receives the count of perturbed pivots. */
 kkt_status kkt_status_sync(kkt_ctx *ctx, kkt_stream stream, int *n_perturbed);
+
+/*
+ * Inertia of A from the last refactorization (options.symmetric = 1): the
+ * numbers of positive and negative pivots of A' = L D L^T (Sec. 3: the
+ * inertia an interior method checks; Sylvester's law of inertia makes them
+ * those of A, since A' = S P A P^T S is congruent to A).  n_perturbed: pivots
+ * replaced by +-tau in that refactorization (counted with the sign they got):
+ * A is then singular or nearly so in the pivot test's sense.  Synchronizes
+ * the stream.  KKT_ERR_STATE without options.symmetric or before a
+ * refactorization.  Any pointer may be NULL.
+ */
+kkt_status kkt_inertia(kkt_ctx *ctx, kkt_stream stream, int *n_pos, int *n_neg, int *n_perturbed);
 
 /* Sizes, byte and flop counts of the analysis (host, no synchronization). */
 kkt_status kkt_get_stats(const kkt_ctx *ctx, kkt_stats *stats);

@@ -204,6 +204,47 @@ class Factor:
         lib().orc_lu_solve_t(self._h, y)
         return y
 
+    def jacobi_solve(self, y, sweeps):
+        """Approximate U^-1 L^-1 y by Jacobi sweeps on each triangular factor
+        (Sec. 6: iterative approximation of the triangular solves, the method
+        of Anzt, Chow and Dongarra 2015).  With L = I + L_s (L_s strictly
+        lower) and U = D + U_s (D its diagonal, U_s strictly upper):
+            w_0 = y,        w_{k+1} = y - L_s w_k,            k < sweeps,
+            z_0 = D^-1 w,   z_{k+1} = D^-1 (w - U_s z_k),     k < sweeps.
+        Each sweep is one sparse product, with no dependency between rows.
+        Since L_s and D^-1 U_s are nilpotent, the result is the exact solve
+        once sweeps + 1 reaches the number of levels of the factor's
+        dependency graph."""
+        return self._jacobi(_f64(y), sweeps, transpose=False)
+
+    def jacobi_solve_t(self, y, sweeps):
+        """The same for A'^T = U^T L^T: Jacobi sweeps on U^T = D + U_s^T, then on
+        L^T = I + L_s^T."""
+        return self._jacobi(_f64(y), sweeps, transpose=True)
+
+    def _jacobi(self, y, sweeps, transpose):
+        L = self.L_csc().tocsr()
+        U = self.U_csc()
+        D = U.diagonal()
+        Us = sp.triu(U, 1, format="csr")
+        if not transpose:
+            w = y.copy()
+            for _ in range(sweeps):
+                w = y - L @ w
+            z = w / D
+            for _ in range(sweeps):
+                z = (w - Us @ z) / D
+            return z
+        UsT = Us.T.tocsr()
+        LT = L.T.tocsr()
+        w = y / D
+        for _ in range(sweeps):
+            w = (y - UsT @ w) / D
+        z = w.copy()
+        for _ in range(sweeps):
+            z = w - LT @ z
+        return z
+
     def L_csc(self):
         return sp.csc_matrix((self.Lx, self.Li, self.Lp), shape=(self.n, self.n))
 
@@ -291,10 +332,18 @@ class Oracle:
         lam[self.perm] = sp_ * z
         return lam
 
+    # Jacobi-sweep approximation of solve() (Sec. 6), same permutation and scaling.
+    def solve_jacobi(self, b, sweeps):
+        sp_ = self.s[self.perm]
+        z = self.F.jacobi_solve(sp_ * _f64(b)[self.perm], sweeps)
+        x = np.empty(self.n)
+        x[self.perm] = sp_ * z
+        return x
+
     def omega(self, b, x):
         return omega(self.n, self.indptr, self.indices, self.values, b, x, self.anorm)
 
-    def refine(self, b, x0=None, tol=1e-14, max_it=20, mode="auto", restart=20):
+    def refine(self, b, x0=None, tol=1e-14, max_it=20, mode="auto", restart=20, sweeps=0):
         """Iterative refinement (Sec. 5.1) to omega <= tol with at most max_it
         solves with the factors.
 
@@ -303,6 +352,10 @@ class Oracle:
         CGS2 orthogonalization (Sec. 5.1).
         mode "auto" (reading): classic, switching to FGMRES for the remaining
         budget once an iteration fails to halve omega.
+        mode "fgmres_jacobi": FGMRES(restart) whose preconditioner applies
+        ``sweeps`` Jacobi sweeps per triangular factor instead of the exact
+        solves (Sec. 6); FGMRES allows a preconditioner that is not an exact
+        inverse (Saad 1993).
         Returns (x, iterations, omega history, converged).
         """
         b = _f64(b)
@@ -322,10 +375,11 @@ class Oracle:
                 w = w_new
                 if mode == "auto" and stalled and w > tol:
                     break
-        if w > tol and it < max_it and mode in ("fgmres", "auto"):
+        if w > tol and it < max_it and mode in ("fgmres", "auto", "fgmres_jacobi"):
+            prec = (lambda v: self.solve_jacobi(v, sweeps)) if mode == "fgmres_jacobi" else self.solve
             while w > tol and it < max_it:
                 m = min(restart, max_it - it)
-                x, used = self._fgmres_cycle(b, x, m, tol)
+                x, used = self._fgmres_cycle(b, x, m, tol, prec)
                 it += used
                 w = self.omega(b, x)
                 hist.append(w)
@@ -333,11 +387,12 @@ class Oracle:
                     break
         return x, it, hist, w <= tol
 
-    def _fgmres_cycle(self, b, x0, m, tol):
-        """One FGMRES(m) cycle (Saad 1993), right preconditioner M^-1 = LU solve,
-        CGS2 (classical Gram-Schmidt applied twice).  Stops early when the
-        least-squares residual estimate meets the scaled tolerance.  Returns
-        (x, preconditioner applications)."""
+    def _fgmres_cycle(self, b, x0, m, tol, prec=None):
+        """One FGMRES(m) cycle (Saad 1993), right preconditioner M^-1 = LU solve
+        (or ``prec``), CGS2 (classical Gram-Schmidt applied twice).  Stops early
+        when the least-squares residual estimate meets the scaled tolerance.
+        Returns (x, preconditioner applications)."""
+        prec = self.solve if prec is None else prec
         n = self.n
         r0 = residual(n, self.indptr, self.indices, self.values, b, x0)
         beta = np.linalg.norm(r0)
@@ -351,7 +406,7 @@ class Oracle:
         bn = np.max(np.abs(b))
         k_used = 0
         for j in range(m):
-            Z[j] = self.solve(V[j])
+            Z[j] = prec(V[j])
             w = A @ Z[j]
             h1 = V[: j + 1] @ w
             w = w - V[: j + 1].T @ h1
@@ -380,6 +435,23 @@ class Oracle:
         k = k_used
         y = np.linalg.solve(np.triu(H[:k, :k]), gvec[:k]) if k else np.zeros(0)
         return x0 + Z[:k].T @ y, k
+
+    def ldlt(self):
+        """(L, D) with A' = L D L^T for symmetric values (Sec. 3 inertia; the
+        MA57 form of Sec. 5.3's CPU baseline).  Plain definition: without row
+        or column exchanges the Doolittle factors of a symmetric matrix satisfy
+        U = D L^T with D = diag(U), so L is the unit lower factor of the LU and
+        D its pivots (perturbed pivots included)."""
+        return self.F.L_csc(), self.F.U_csc().diagonal().copy()
+
+    def inertia(self):
+        """(n_pos, n_neg) of A for symmetric values: the signs of the pivots D
+        of A' = L D L^T.  A' = S P A P^T S is congruent to A, so by Sylvester's
+        law of inertia these are the numbers of positive and negative
+        eigenvalues of A (when no pivot was perturbed)."""
+        _, D = self.ldlt()
+        neg = int(np.sum(D < 0))
+        return self.n - neg, neg
 
     def adjoint(self, x, g):
         """Backward of x = A^-1 b for the upstream gradient g:

@@ -24,7 +24,7 @@ KKT_ERR_INTERNAL = 9
 KKT_WARN_PERTURBED = 100
 
 ORDER_AMD, ORDER_NATURAL, ORDER_USER = 0, 1, 2
-REFINE_CLASSIC, REFINE_FGMRES, REFINE_AUTO = 0, 1, 2
+REFINE_CLASSIC, REFINE_FGMRES, REFINE_AUTO, REFINE_FGMRES_JACOBI = 0, 1, 2, 3
 
 
 class Options(C.Structure):
@@ -49,6 +49,8 @@ class Options(C.Structure):
         ("poll_ns_max", C.c_int),
         ("unpublished_row", C.c_int),
         ("refactor_big_warps", C.c_int),
+        ("symmetric", C.c_int),
+        ("jacobi_sweeps", C.c_int),
     ]
 
 
@@ -129,6 +131,8 @@ SIGNATURES = {
     "kkt_queue_status_sync": (C.c_int, [_vp, _vp, _ip]),
     "kkt_scaled_residual_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "kkt_probe_fma_tflops": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "kkt_inertia": (C.c_int, [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "kkt_solve_jacobi": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
 }
 
 _lib = None

@@ -26,8 +26,10 @@
 
 namespace kkt {
 
+// ST_NEGATIVE / ST_PERT_LAST: negative and perturbed pivots of the last
+// symmetric (LDL^T) refactorization, cleared at its start (the inertia).
 enum StatusSlot { ST_PERTURBED = 0, ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_ABORT = 3, ST_INTERNAL = 4,
-                  ST_WORDS = 8 };
+                  ST_NEGATIVE = 5, ST_PERT_LAST = 6, ST_WORDS = 8 };
 
 // Norms kept on the device as the bit patterns of non-negative doubles, so
 // that atomicMax on unsigned 64-bit integers orders them correctly.
@@ -105,6 +107,7 @@ struct RunCfg {
     int nbig;                    // k_refactor: big warps per CTA (warps 0 .. nbig-1; 0 = none)
     int smem_cols;               // k_refactor: 1 if the row's columns are staged too (no update maps)
     int staged;                  // k_refactor: 1 = pivot rows fed through each warp's staging ring
+    int symmetric;               // k_refactor: 1 = LDL^T of symmetric values (refactor_row_sym)
     int warp_bytes_big;          // k_refactor: shared-memory bytes of a big / small warp's block
     int warp_bytes_small;
     void *scratch;               // per-warp global rows for rows longer than cap

@@ -514,7 +514,9 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                     if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
                     pv = (aii < 0.0) ? -tau : tau;
                     atomicAdd(rc.status + ST_PERTURBED, 1);
+                    atomicAdd(rc.status + ST_PERT_LAST, 1);
                 }
+                if (pv < 0.0) atomicAdd(rc.status + ST_NEGATIVE, 1);
                 w[dp] = (T)pv;
             }
             __syncwarp();
@@ -732,7 +734,9 @@ __device__ __forceinline__ void refactor_row_staged(const DevPattern &P, const R
             if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
             pv = (aii < 0.0) ? -tau : tau;
             atomicAdd(rc.status + ST_PERTURBED, 1);
+            atomicAdd(rc.status + ST_PERT_LAST, 1);
         }
+        if (pv < 0.0) atomicAdd(rc.status + ST_NEGATIVE, 1);
         w[dp] = (T)pv;
     }
     __syncwarp();
@@ -746,6 +750,190 @@ __device__ __forceinline__ void refactor_row_staged(const DevPattern &P, const R
         LUT[P.tpos[rb + t]] = w[t];
     }
 }
+
+// ---------------------------------------------------------------------------
+// Symmetric values: LDL^T through the same storage (options.symmetric).
+//
+// For a symmetric A' the Doolittle factors satisfy L = U^T D^-1 with D the
+// pivots (A' = L D L^T, the MA57 form of the paper's CPU baseline, Sec. 5.3;
+// Sec. 3 on inertia).  Row i then needs no elimination of its own L part:
+// its multipliers are l(i,d) = u(d,i) / u(d,d), entries of rows below it that
+// are already published, and only its U part is reduced,
+//     u(i,j) = a'(i,j) - sum_d l(i,d) u(d,j),   j >= i,
+// over the tail U(d, >= i) of each pivot row.  The pivot steps of a row are
+// independent of each other (no multiplier waits on an earlier step), each
+// touches only the part of U(d,:) at or right of column i, and the flops are
+// half those of LU.  L is still written (l(i,d) into row i's L slots), so the
+// solves and exports are those of the LU path.  The lower triangle of the
+// values is not read: the factorization is that of the symmetric matrix with
+// A's upper triangle.  The pivot signs give the inertia (Sylvester's law:
+// S P A P^T S is congruent to A).
+template <typename T>
+__device__ __forceinline__ void refactor_row_sym(const DevPattern &P, const RunCfg &rc,
+                                                 const double *__restrict__ aval,
+                                                 const double *__restrict__ sp, T *LU, T *LUT, T *rcp,
+                                                 double tau, int i, T *sval, int cap,
+                                                 unsigned char *ring, int gw, int lane) {
+    using S = Stage<T>;
+    constexpr int UJ = S::SB / 32;
+    const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
+    const int ulen = len - dp;                         // U part, diagonal first
+    // the row buffer holds the U part only; each multiplier l(i,d) goes to
+    // its L slot at once (the address needs no load) and to the transposed
+    // factor at the end
+    T *w = ulen <= cap ? sval : reinterpret_cast<T *>(rc.scratch) + (size_t)gw * rc.scratch_stride;
+    const double si = sp[i];
+    for (int t = lane; t < ulen; t += 32) {
+        const int k = P.src[rb + dp + t];
+        w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + dp + t]] * aval[k] : 0.0);
+    }
+    __syncwarp();
+    if (dp > 0) {
+        int pt = 0, pb = 0, c0 = 0;
+        int md = 0, mub = 0, mue = 0, mts = 0, nd = 0, nub = 0, nue = 0, nts = 0;
+        unsigned mmo = 0, nmo = 0;
+        auto load_meta = [&](int t0, int &d_, int &ub_, int &ue_, int &ts_, unsigned &mo_) {
+            d_ = ub_ = ue_ = ts_ = 0;
+            mo_ = 0;
+            if (t0 + lane < dp) {
+                d_ = P.lu_ci[rb + t0 + lane];
+                ub_ = P.diag[d_];
+                ue_ = P.lu_rp[d_ + 1];
+                ts_ = P.tpos[rb + t0 + lane];           // slot of u(d,i) in row d
+                mo_ = P.upd_off[rb + t0 + lane];
+            }
+        };
+        load_meta(0, md, mub, mue, mts, mmo);
+        load_meta(32, nd, nub, nue, nts, nmo);
+        auto issue = [&](int unit) {
+            unsigned char *slot = ring + (unit % S::STAGES) * S::SLOT;
+            if (pt < dp) {
+                if (pt - c0 >= 32) {
+                    c0 += 32;
+                    md = nd; mub = nub; mue = nue; mts = nts; mmo = nmo;
+                    load_meta(c0 + 32, nd, nub, nue, nts, nmo);
+                }
+                const int k = pt - c0;
+                const int d = __shfl_sync(FULL, md, k), ub = __shfl_sync(FULL, mub, k);
+                const int ue = __shfl_sync(FULL, mue, k), ts = __shfl_sync(FULL, mts, k);
+                const unsigned mo = __shfl_sync(FULL, mmo, k);
+                const int u0 = ts + pb * S::SB;         // the tail U(d, >= i), u(d,i) first
+                const int cnt = min(S::SB, ue - u0);
+                const int last = (u0 + S::SB >= ue);
+                const int vo = u0 & (S::VE - 1);
+                const unsigned mstart = mo + (unsigned)(u0 - ub - 1);
+                const int mo2 = (int)(mstart & 7u);
+                T *sv = reinterpret_cast<T *>(slot);
+                unsigned short *sm = reinterpret_cast<unsigned short *>(slot + S::VAL_BYTES);
+                T *sr = reinterpret_cast<T *>(slot + S::VAL_BYTES + S::MAP_BYTES);
+                int *desc = reinterpret_cast<int *>(slot + S::VAL_BYTES + S::MAP_BYTES + 16);
+                const T *vsrc = LU + (u0 - vo);
+                const int vch = (vo + cnt + S::VE - 1) / S::VE;
+                for (int q = lane; q < vch; q += 32) cp_async16(sv + q * S::VE, vsrc + q * S::VE);
+                const unsigned short *msrc = P.upd_map + (mstart - (unsigned)mo2);
+                const int mch = (mo2 + cnt + 7) / 8;
+                for (int q = lane; q < mch; q += 32) cp_async16(sm + q * 8, msrc + q * 8);
+                if (pb == 0 && lane == 0) cp_async_word(sr, rcp + d);
+                if (lane == 0) {
+                    desc[0] = pt; desc[1] = u0; desc[2] = cnt; desc[3] = vo;
+                    desc[4] = mo2; desc[5] = d; desc[6] = (pb == 0) | (last << 1);
+                }
+                if (last) { pt++; pb = 0; } else { pb++; }
+            }
+            cp_async_commit();
+        };
+        for (int q = 0; q < S::STAGES - 1; q++) issue(q);
+        T l = T(0);
+        for (int unit = 0;; unit++) {
+            __syncwarp();
+            issue(unit + S::STAGES - 1);
+            cp_async_wait<S::STAGES - 1>();
+            __syncwarp();
+            unsigned char *slot = ring + (unit % S::STAGES) * S::SLOT;
+            const T *sv = reinterpret_cast<const T *>(slot);
+            const unsigned short *sm = reinterpret_cast<const unsigned short *>(slot + S::VAL_BYTES);
+            const T *sr = reinterpret_cast<const T *>(slot + S::VAL_BYTES + S::MAP_BYTES);
+            const int *desc = reinterpret_cast<const int *>(slot + S::VAL_BYTES + S::MAP_BYTES + 16);
+            const int t = desc[0], u0 = desc[1], cnt = desc[2], vo = desc[3], mo2 = desc[4], d = desc[5];
+            const int flags = desc[6];
+            int lo[UJ];
+            T uv[UJ];
+            unsigned need = 0;
+#pragma unroll
+            for (int q = 0; q < UJ; q++) {
+                const int j = 32 * q + lane;
+                lo[q] = -1;
+                uv[q] = T(0);
+                if (j < cnt) {
+                    lo[q] = (int)sm[mo2 + j] - dp;
+                    uv[q] = sv[vo + j];
+                    if (is_marker(uv[q])) need |= 1u << q;
+                }
+            }
+            if (__any_sync(FULL, need != 0)) {
+#pragma unroll
+                for (int q = 0; q < UJ; q++)
+                    if ((need >> q) & 1u) uv[q] = ld_relaxed_v(LU + (u0 + 32 * q + lane));
+                need = 0;
+#pragma unroll
+                for (int q = 0; q < UJ; q++)
+                    if (lo[q] >= 0 && is_marker(uv[q])) need |= 1u << q;
+                if (__any_sync(FULL, need != 0)) {
+#pragma unroll
+                    for (int q = 0; q < UJ; q++) {
+                        const bool nq = (need >> q) & 1u;
+                        const T v = warp_wait_load(rc, LU + (nq ? u0 + 32 * q + lane : u0), nq, lane);
+                        if (nq) uv[q] = v;
+                    }
+                }
+            }
+            if (flags & 1) {                            // first block: l(i,d) = u(d,i) / u(d,d)
+                T r = sr[0];
+                if (is_marker(r)) {
+                    r = ld_relaxed_v(rcp + d);
+                    if (__any_sync(FULL, lane == 0 && is_marker(r))) {
+                        const T w0 = warp_wait_load(rc, rcp + d, lane == 0, lane);
+                        if (lane == 0) r = w0;
+                    }
+                    r = __shfl_sync(FULL, r, 0);
+                }
+                l = __shfl_sync(FULL, uv[0], 0) * r;     // lane 0, q 0 holds u(d,i)
+                if (lane == 0) LU[rb + t] = l;
+            }
+            T x[UJ];
+#pragma unroll
+            for (int q = 0; q < UJ; q++) x[q] = lo[q] >= 0 ? w[lo[q]] : T(0);
+#pragma unroll
+            for (int q = 0; q < UJ; q++)
+                if (lo[q] >= 0) w[lo[q]] = x[q] - l * uv[q];
+            if ((flags & 2) && t + 1 == dp) break;
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+    }
+    // pivot test in FP64 (perturb to sign(a_ii) tau and count), sign for the inertia
+    if (lane == 0) {
+        double pv = (double)w[0];
+        if (!(fabs(pv) >= tau) || isinf(pv)) {
+            const int k = P.src[rb + dp];
+            const double aii = (k >= 0) ? si * si * aval[k] : 0.0;
+            if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
+            pv = (aii < 0.0) ? -tau : tau;
+            atomicAdd(rc.status + ST_PERTURBED, 1);
+            atomicAdd(rc.status + ST_PERT_LAST, 1);
+        }
+        if (pv < 0.0) atomicAdd(rc.status + ST_NEGATIVE, 1);
+        w[0] = (T)pv;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        LU[rb + dp] = w[0];
+        if (i != rc.unpublished_row) publish(rc, rcp + i, T(1) / w[0]);
+    }
+    for (int t = 1 + lane; t < ulen; t += 32) publish(rc, LU + (rb + dp + t), w[t]);
+    for (int t = lane; t < ulen; t += 32) LUT[P.tpos[rb + dp + t]] = w[t];
+    for (int t = lane; t < dp; t += 32) LUT[P.tpos[rb + t]] = LU[rb + t];   // lane 0's stores, seen
+}                                                                       // after the warp's syncs
 
 // Shared memory of k_refactor: warps 0 .. nbig-1 of every CTA ("big" warps)
 // own a row buffer of cap_big entries, the others one of cap entries; the
@@ -791,7 +979,9 @@ k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const doubl
             if (slot >= count) break;
             const int row = order[slot];
             trace_mark(rc, 0, row, 0, lane);
-            if (rc.staged)
+            if (rc.symmetric)
+                refactor_row_sym<T>(P, rc, aval, sp, LU, LUT, rcp, tau, row, sval, cap, ring, gw, lane);
+            else if (rc.staged)
                 refactor_row_staged<T>(P, rc, aval, sp, LU, LUT, rcp, tau, row, sval, cap, ring, gw, lane);
             else
                 refactor_row<T>(P, rc, aval, sp, LU, LUT, rcp, tau, row, sval, scol, cap, gw, lane);
@@ -1742,6 +1932,53 @@ __global__ void k_vscale(double *__restrict__ v, const double *__restrict__ w, d
     if (i < n) v[i] = w[i] * s;
 }
 
+// ---------------------------------------------------------------------------
+// Jacobi sweeps for approximate triangular solves (Sec. 6: iterative
+// approximation of the triangular solves, after Anzt, Chow and Dongarra 2015).
+// One sweep of one factor, 8 lanes per row of the factor storage F (LU, or
+// its transposed copy LUT for the transposed system):
+//   out[i] = (rhs[i] - sum over the slots on one side of the diagonal of
+//             F[t] * in[col t]) * (SCALE ? 1 / pivot_i : 1)
+// RIGHT: the slots right of the diagonal (U, or L^T), else left (L, or U^T).
+// in == nullptr is the zero vector (the first term of the iteration).  Every
+// row is independent: a sweep is one sparse product with no dependency chain.
+template <typename T, bool RIGHT, bool SCALE>
+__global__ void k_jacobi(DevPattern P, const T *__restrict__ F, const T *__restrict__ rcp,
+                         const T *__restrict__ rhs, const T *__restrict__ in, T *__restrict__ out) {
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int sub = threadIdx.x & 7;
+    T acc = T(0);
+    if (r < P.n && in != nullptr) {
+        const int tb = RIGHT ? P.diag[r] + 1 : P.lu_rp[r];
+        const int te = RIGHT ? P.lu_rp[r + 1] : P.diag[r];
+        for (int t = tb + sub; t < te; t += 8) acc += F[t] * in[P.lu_ci[t]];
+    }
+    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (r < P.n && sub == 0) {
+        T v = rhs[r] - acc;
+        if (SCALE) v *= rcp[r];
+        out[r] = v;
+    }
+}
+
+// entry and exit of an approximate solve: c = S P b (factor precision), and
+// x[perm[i]] = s_i z_i (or +=, for refinement)
+template <typename T>
+__global__ void k_perm_in(DevPattern P, const double *__restrict__ sp, const double *__restrict__ b,
+                          T *__restrict__ c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.n) c[i] = (T)(sp[i] * b[P.perm[i]]);
+}
+template <typename T>
+__global__ void k_perm_out(DevPattern P, const double *__restrict__ sp, const T *__restrict__ z,
+                           double *__restrict__ x, int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.n) {
+        const double v = sp[i] * (double)z[i];
+        if (accumulate) x[P.perm[i]] += v; else x[P.perm[i]] = v;
+    }
+}
+
 // ===========================================================================
 // Batched same-pattern systems (batch innermost): value k of system s sits at
 // k * B + s, vector entry i of system s at i * B + s.  Work items are (row or
@@ -2127,6 +2364,8 @@ void kkt_default_options(kkt_options *o) {
     o->unpublished_row = -1;
     o->poll_ns_max = 0;
     o->refactor_big_warps = 0;
+    o->symmetric = 0;
+    o->jacobi_sweeps = 8;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -2286,6 +2525,7 @@ static kkt_status upload(kkt_ctx *c) {
         c->rc.cap_big = cap_big;
         c->rc.smem_cols = mapped ? 0 : 1;
         c->rc.staged = staged ? 1 : 0;
+        c->rc.symmetric = (staged && c->opt.symmetric) ? 1 : 0;   // LDL^T needs the update maps
         c->rc.warp_bytes_big = (int)warp_bytes(cap_big);
         c->rc.warp_bytes_small = (int)warp_bytes(cap);
         c->rsmem = (size_t)nbig * warp_bytes(cap_big) + (size_t)(nw - nbig) * warp_bytes(cap);
@@ -2599,7 +2839,8 @@ static kkt_status upload(kkt_ctx *c) {
             return KKT_ERR_CUDA;
         }
     }
-    if (c->opt.refine_mode == KKT_REFINE_FGMRES || c->opt.refine_mode == KKT_REFINE_AUTO) {
+    if (c->opt.refine_mode == KKT_REFINE_FGMRES || c->opt.refine_mode == KKT_REFINE_AUTO ||
+        c->opt.refine_mode == KKT_REFINE_FGMRES_JACOBI) {
         const int m = std::min(c->opt.fgmres_restart, 63);
         c->kry_m = m;
         c->kry_blocks = std::max(1, std::min(1024, (n + 255) / 256));
@@ -2709,6 +2950,8 @@ kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_
     if (!c) return KKT_ERR_ALLOC;
     if (opt) c->opt = *opt; else kkt_default_options(&c->opt);
     if (c->opt.fgmres_restart < 1 || c->opt.max_refine < 0 || c->opt.spin_limit < 1 ||
+        c->opt.refine_mode < KKT_REFINE_CLASSIC || c->opt.refine_mode > KKT_REFINE_FGMRES_JACOBI ||
+        c->opt.jacobi_sweeps < 0 ||
         c->opt.max_batch < 1 || c->opt.cta_warps < 0 || c->opt.refactor_ctas < 0 ||
         c->opt.solve_ctas < 0) {
         g_last_error = "invalid option";
@@ -2853,6 +3096,7 @@ kkt_status kkt_refactor(kkt_ctx *c, const double *values_dev, kkt_stream stream)
     c->values = values_dev;
     const int n = c->an.n;
     CK(cudaMemsetAsync(c->d_norms, 0, NM_WORDS * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(c->d_status + ST_NEGATIVE, 0, 2 * sizeof(int), s));   // this refactorization's inertia
     k_scale<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, values_dev, c->d_s, c->d_sp, c->d_norms,
                                                      c->d_status, c->opt.equilibrate);
     CK(cudaGetLastError());
@@ -2876,6 +3120,84 @@ static kkt_status solve_any(kkt_ctx *c, const double *b, double *x, int accumula
                                   : launch_solve_t<double>(c, b, x, accumulate, s);
     return c->opt.factor_fp32 ? launch_solve<float>(c, b, x, accumulate, s)
                               : launch_solve<double>(c, b, x, accumulate, s);
+}
+
+// Approximate solve by Jacobi sweeps (k_jacobi): `sweeps` sweeps on each
+// triangular factor; the work vectors are three n-vectors of the context's
+// scratch (c, then ping-pong).  A' = L U: L stage then U stage; A'^T = U^T L^T
+// on the transposed factor: U^T stage (scaled) then L^T stage.
+template <typename T>
+static kkt_status launch_jacobi(kkt_ctx *c, const double *b, double *x, int accumulate, int transpose,
+                                int sweeps, cudaStream_t s) {
+    const int n = c->an.n;
+    T *buf[3] = {(T *)c->d_y, (T *)c->d_y + n, (T *)c->d_y + 2 * (size_t)n};
+    const T *F = (const T *)(transpose ? c->d_lut : c->d_lu), *R = (const T *)c->d_rcp;
+    const int gb = blocks_for(8LL * n, 256), nb = blocks_for(n, 256);
+    k_perm_in<T><<<nb, 256, 0, s>>>(c->P, c->d_sp, b, buf[0]);
+    CK(cudaGetLastError());
+    c->launches++;
+    // first stage: unit L (left slots, no scale) or U^T (left slots, scaled)
+    int cur = 0;                                // buffer holding the current iterate
+    if (transpose) {                            // w_0 = D^-1 c into buf[1]
+        k_jacobi<T, false, true><<<gb, 256, 0, s>>>(c->P, F, R, buf[0], nullptr, buf[1]);
+        CK(cudaGetLastError());
+        c->launches++;
+        cur = 1;
+    }
+    for (int k = 0; k < sweeps; k++) {
+        const int nxt = (cur == 1) ? 2 : 1;
+        if (transpose) k_jacobi<T, false, true><<<gb, 256, 0, s>>>(c->P, F, R, buf[0], buf[cur], buf[nxt]);
+        else k_jacobi<T, false, false><<<gb, 256, 0, s>>>(c->P, F, R, buf[0], buf[cur], buf[nxt]);
+        CK(cudaGetLastError());
+        c->launches++;
+        cur = nxt;
+    }
+    // second stage on w = buf[cur]: U (right slots, scaled) or unit L^T (right, no scale)
+    const int w = cur;
+    int z = -1;
+    int fa = (w == 0) ? 1 : 0, fb = (w == 2) ? 1 : 2;   // the two buffers other than w
+    if (!transpose) {                           // z_0 = D^-1 w
+        k_jacobi<T, true, true><<<gb, 256, 0, s>>>(c->P, F, R, buf[w], nullptr, buf[fa]);
+        CK(cudaGetLastError());
+        c->launches++;
+        z = fa;
+    } else {
+        z = w;                                  // z_0 = w
+    }
+    for (int k = 0; k < sweeps; k++) {
+        const int nxt = (z == fa) ? fb : fa;
+        if (transpose) k_jacobi<T, true, false><<<gb, 256, 0, s>>>(c->P, F, R, buf[w], buf[z], buf[nxt]);
+        else k_jacobi<T, true, true><<<gb, 256, 0, s>>>(c->P, F, R, buf[w], buf[z], buf[nxt]);
+        CK(cudaGetLastError());
+        c->launches++;
+        z = nxt;
+    }
+    k_perm_out<T><<<nb, 256, 0, s>>>(c->P, c->d_sp, buf[z], x, accumulate);
+    CK(cudaGetLastError());
+    c->launches++;
+    return KKT_OK;
+}
+
+static kkt_status jacobi_any(kkt_ctx *c, const double *b, double *x, int accumulate, int transpose, int sweeps,
+                             cudaStream_t s) {
+    return c->opt.factor_fp32 ? launch_jacobi<float>(c, b, x, accumulate, transpose, sweeps, s)
+                              : launch_jacobi<double>(c, b, x, accumulate, transpose, sweeps, s);
+}
+
+// the preconditioner of FGMRES: the exact triangular solves, or Jacobi sweeps
+static kkt_status precond_any(kkt_ctx *c, const double *b, double *x, int transpose, cudaStream_t s) {
+    if (c->opt.refine_mode == KKT_REFINE_FGMRES_JACOBI)
+        return jacobi_any(c, b, x, 0, transpose, c->opt.jacobi_sweeps, s);
+    return solve_any(c, b, x, 0, transpose, s);
+}
+
+kkt_status kkt_solve_jacobi(kkt_ctx *c, const double *b_dev, double *x_dev, int sweeps, int transpose,
+                            kkt_stream stream) {
+    REQUIRE_DEVICE(c);
+    if (!b_dev || !x_dev || b_dev == x_dev || sweeps < 0) return KKT_ERR_ARG;
+    if (!c->factored) return KKT_ERR_STATE;
+    DeviceGuard g(c->dev);
+    return jacobi_any(c, b_dev, x_dev, 0, transpose ? 1 : 0, sweeps, (cudaStream_t)stream);
 }
 
 kkt_status kkt_solve(kkt_ctx *c, const double *b_dev, double *x_dev, kkt_stream stream) {
@@ -2968,7 +3290,7 @@ static kkt_status fgmres_cycle(kkt_ctx *c, const double *b, double *x, double to
     int k_used = 0;
     for (int j = 0; j < m; j++) {
         double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
-        if ((st = solve_any(c, vj, zj, 0, transpose, s))) return st;
+        if ((st = precond_any(c, vj, zj, transpose, s))) return st;
         k_spmv<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, c->values, zj, w, transpose);
         CK(cudaGetLastError());
         c->launches++;
@@ -3057,7 +3379,8 @@ static kkt_status refine_any(kkt_ctx *c, const double *b, double *x, double tol,
             if (mode == KKT_REFINE_AUTO && !(w <= 0.5 * prev) && !(w <= tol)) break;   // stalled
         }
     }
-    if ((mode == KKT_REFINE_FGMRES || mode == KKT_REFINE_AUTO) && c->d_krylov) {
+    if ((mode == KKT_REFINE_FGMRES || mode == KKT_REFINE_AUTO || mode == KKT_REFINE_FGMRES_JACOBI) &&
+        c->d_krylov) {
         while (!(w <= tol) && it < max_it && std::isfinite(w)) {
             const double an = host_norm(c, transpose ? NM_A1NORM : NM_ANORM);
             int used = 0;
@@ -3714,12 +4037,31 @@ kkt_status kkt_status_sync(kkt_ctx *c, kkt_stream stream, int *n_perturbed) {
     int st[ST_WORDS];
     CK(cudaStreamSynchronize(s));
     CK(cudaMemcpy(st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
-    CK(cudaMemset(c->d_status, 0, sizeof(st)));
+    // the accumulated conditions are cleared; the inertia counters of the last
+    // refactorization (ST_NEGATIVE, ST_PERT_LAST) stay for kkt_inertia
+    CK(cudaMemset(c->d_status, 0, ST_NEGATIVE * sizeof(int)));
     if (n_perturbed) *n_perturbed = st[ST_PERTURBED];
     if (st[ST_INTERNAL]) { g_last_error = "factor pattern not closed under fill"; return KKT_ERR_INTERNAL; }
     if (st[ST_TIMEOUT]) return KKT_ERR_TIMEOUT;
     if (st[ST_NONFINITE]) return KKT_ERR_NONFINITE;
     if (st[ST_PERTURBED]) return KKT_WARN_PERTURBED;
+    return KKT_OK;
+}
+
+kkt_status kkt_inertia(kkt_ctx *c, kkt_stream stream, int *n_pos, int *n_neg, int *n_perturbed) {
+    REQUIRE_DEVICE(c);
+    if (!c->opt.symmetric) {
+        g_last_error = "kkt_inertia: the context was not created for symmetric values";
+        return KKT_ERR_STATE;
+    }
+    if (!c->factored) return KKT_ERR_STATE;
+    DeviceGuard g(c->dev);
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    int st[ST_WORDS];
+    CK(cudaMemcpy(st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (n_neg) *n_neg = st[ST_NEGATIVE];
+    if (n_pos) *n_pos = c->an.n - st[ST_NEGATIVE];
+    if (n_perturbed) *n_perturbed = st[ST_PERT_LAST];
     return KKT_OK;
 }
 

@@ -16,7 +16,8 @@ from . import _capi
 from ._capi import check
 
 _ORDER = {"amd": _capi.ORDER_AMD, "natural": _capi.ORDER_NATURAL, "user": _capi.ORDER_USER}
-_REFINE = {"classic": _capi.REFINE_CLASSIC, "fgmres": _capi.REFINE_FGMRES, "auto": _capi.REFINE_AUTO}
+_REFINE = {"classic": _capi.REFINE_CLASSIC, "fgmres": _capi.REFINE_FGMRES, "auto": _capi.REFINE_AUTO,
+           "fgmres_jacobi": _capi.REFINE_FGMRES_JACOBI}
 
 
 def _ptr(t: torch.Tensor):
@@ -44,7 +45,7 @@ class KKTSolver:
                  perm=None, refine_mode="classic", tol=1e-14, max_refine=20,
                  pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
                  solve_ctas=0, update_map_budget=0, trace=False, max_batch=1, unpublished_row=-1,
-                 poll_ns_max=0, refactor_big_warps=0, device=0):
+                 poll_ns_max=0, refactor_big_warps=0, symmetric=False, jacobi_sweeps=8, device=0):
         self._lib = _capi.load()
         self.n = int(n)
         self._rp = _i32(indptr)
@@ -73,6 +74,8 @@ class KKTSolver:
         opt.unpublished_row = int(unpublished_row)
         opt.poll_ns_max = int(poll_ns_max)
         opt.refactor_big_warps = int(refactor_big_warps)
+        opt.symmetric = int(bool(symmetric))
+        opt.jacobi_sweeps = int(jacobi_sweeps)
         self.device = None if device is None else torch.device("cuda", int(device)) if not isinstance(
             device, torch.device) else device
         opt.device = -1 if self.device is None else (self.device.index or 0)
@@ -132,6 +135,14 @@ class KKTSolver:
         check(self._lib.kkt_export_scaling(self._h, _ptr(out), _stream(stream)), "kkt_export_scaling")
         return out
 
+    def inertia(self, stream=None):
+        """(n_pos, n_neg, n_perturbed) of the last refactorization of a context
+        created with symmetric=True (kkt_inertia); synchronises the stream."""
+        p, m, z = C.c_int(0), C.c_int(0), C.c_int(0)
+        check(self._lib.kkt_inertia(self._h, _stream(stream), C.byref(p), C.byref(m), C.byref(z)),
+              "kkt_inertia")
+        return p.value, m.value, z.value
+
     def status(self, stream=None):
         """(status code, perturbed-pivot count); synchronises the stream."""
         k = C.c_int(0)
@@ -157,6 +168,15 @@ class KKTSolver:
         self._vec(b, "b")
         x = torch.empty_like(b) if out is None else out
         check(self._lib.kkt_solve(self._h, _ptr(b), _ptr(x), _stream(stream)), "kkt_solve")
+        return x
+
+    def solve_jacobi(self, b: torch.Tensor, sweeps: int, transpose=False, out=None, stream=None) -> torch.Tensor:
+        """Approximate solve by ``sweeps`` Jacobi sweeps per triangular factor
+        (kkt_solve_jacobi)."""
+        self._vec(b, "b")
+        x = torch.empty_like(b) if out is None else out
+        check(self._lib.kkt_solve_jacobi(self._h, _ptr(b), _ptr(x), int(sweeps), int(bool(transpose)),
+                                         _stream(stream)), "kkt_solve_jacobi")
         return x
 
     def solve_transpose(self, g: torch.Tensor, out=None, stream=None) -> torch.Tensor:

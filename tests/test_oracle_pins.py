@@ -492,3 +492,137 @@ def test_oracle_norm_inf_matches_dense_numpy(seed):
     rho = b - A @ x
     want = np.linalg.norm(rho, np.inf) / (ref * np.linalg.norm(x, np.inf) + np.linalg.norm(b, np.inf))
     assert oracle.omega(n, rp, ci, v, b, x) == want
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_oracle_inertia_matches_dense_eigenvalues(seed):
+    """Sylvester's law of inertia: the pivot signs of A' = L D L^T (A' = S P A
+    P^T S, congruent to A) equal the eigenvalue signs of A.  On a small KKT
+    matrix (quasi-definite: n_x + ... positive, the constraint rows negative)
+    and on a random symmetric indefinite matrix, against numpy.linalg.eigvalsh."""
+    s = kkt_sequence(12, 16, 3, seed=seed, steps=2, W=3.0)
+    A = s.csr(1)
+    p = oracle.min_degree(s.n, s.indptr, s.indices)
+    o = oracle.Oracle(s.n, s.indptr, s.indices, A.data, p)
+    assert o.F.n_perturbed == 0
+    ev = np.linalg.eigvalsh(A.toarray())
+    assert o.inertia() == (int(np.sum(ev > 0)), int(np.sum(ev < 0)))
+    # random symmetric indefinite with a strong diagonal of random signs
+    n = 40
+    rp, ci = random_sparse_pattern(n, 0.1, seed)
+    M = sp.csr_matrix((np.random.default_rng(seed).standard_normal(ci.size), ci, rp), shape=(n, n))
+    M = (M + M.T).tocsr()
+    M.setdiag(np.random.default_rng(seed + 9).choice([-1.0, 1.0], n) * (3.0 + np.abs(M).sum(axis=1).A1))
+    M = M.tocsr(); M.sort_indices()
+    perm = np.random.default_rng(seed).permutation(n).astype(np.int32)
+    o = oracle.Oracle(n, M.indptr, M.indices, M.data, perm)
+    ev = np.linalg.eigvalsh(M.toarray())
+    assert o.inertia() == (int(np.sum(ev > 0)), int(np.sum(ev < 0)))
+
+
+def test_oracle_ldlt_is_lu_of_symmetric_matrix():
+    """For symmetric A', U = D L^T: every U entry equals the pivot times the
+    mirrored L entry, to rounding (bounded by the oracle's running error
+    bounds of both entries), on the 200-bus KKT (n = 1,400)."""
+    s = config_sequence(0)
+    k = 9
+    A = s.csr(k)
+    p = oracle.min_degree(s.n, s.indptr, s.indices)
+    o = oracle.Oracle(s.n, s.indptr, s.indices, A.data, p)
+    L, D = o.ldlt()
+    U = o.F.U_csc().tocsr()
+    Lt = L.T.tocsr()
+    Ue = sp.csr_matrix((o.F.Ue, o.F.Ui, o.F.Up), shape=(s.n, s.n)).tocsc().T.tocsc().T  # same layout as U
+    DLt = sp.diags(D) @ Lt
+    diff = abs(sp.triu(U, 1) - sp.triu(DLt, 1))
+    Ub = sp.csc_matrix((o.F.Ue, o.F.Ui, o.F.Up), shape=(s.n, s.n))
+    Lb = sp.csc_matrix((o.F.Le, o.F.Li, o.F.Lp), shape=(s.n, s.n))
+    bound = sp.triu(Ub, 1) + sp.diags(np.abs(D)) @ Lb.T.tocsr() + sp.diags(Ub.diagonal()) @ abs(Lt)
+    d = diff.toarray(); bnd = 4 * bound.toarray()
+    assert np.all(d <= bnd + 1e-300)
+
+
+def _dense_ldlt(A):
+    """Textbook LDL^T without pivoting: d_j = a_jj - sum_k l_jk^2 d_k,
+    l_ij = (a_ij - sum_k l_ik l_jk d_k) / d_j."""
+    n = A.shape[0]
+    L = np.eye(n)
+    d = np.zeros(n)
+    for j in range(n):
+        d[j] = A[j, j] - np.sum(L[j, :j] ** 2 * d[:j])
+        for i in range(j + 1, n):
+            L[i, j] = (A[i, j] - np.sum(L[i, :j] * L[j, :j] * d[:j])) / d[j]
+    return L, d
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_oracle_ldlt_matches_dense_textbook_ldlt(seed):
+    """The oracle's (L, D) against the textbook dense LDL^T of A' = S P A P^T S
+    on a small KKT matrix (D_x, D_s within [0.1, 10]).  Both compute the same
+    sums in different orders; each entry differs from the exact one by at most
+    the oracle's running error bound E of that entry (first order, any
+    summation order), so they agree within 2 E (the -1e-8 regularization block
+    still cancels several digits in the last pivots)."""
+    s = kkt_sequence(10, 13, 2, seed=seed, steps=2, W=1.0)
+    A = s.csr(1)
+    p = oracle.min_degree(s.n, s.indptr, s.indices)
+    o = oracle.Oracle(s.n, s.indptr, s.indices, A.data, p)
+    Ap = oracle.permuted_matrix(s.n, s.indptr, s.indices, A.data, p, o.s)
+    Apd = sp.csc_matrix((Ap[2], Ap[1], Ap[0]), shape=(s.n, s.n)).toarray()
+    Lr, dr = _dense_ldlt(Apd)
+    L, D = o.ldlt()
+    Ue = sp.csc_matrix((o.F.Ue, o.F.Ui, o.F.Up), shape=(s.n, s.n)).diagonal()
+    Le = sp.csc_matrix((o.F.Le, o.F.Li, o.F.Lp), shape=(s.n, s.n)).toarray()
+    assert np.all(np.abs(D - dr) <= 2 * Ue + 1e-15 * np.abs(dr))
+    assert np.all(np.abs(L.toarray() + np.eye(s.n) - Lr) <= 2 * Le + 1e-15 * np.abs(Lr))
+
+
+def test_oracle_jacobi_sweeps_exact_at_level_count():
+    """L_s and D^-1 U_s are nilpotent: with m nodes on the longest dependency
+    chain (m = max level + 1), (L_s)^m = 0, so m - 1 = max level sweeps give
+    the exact triangular solves (to rounding); three sweeps fewer leave a visible
+    error.  Checked for A' and A'^T against the oracle's own substitution
+    solves (the levels are pinned against brute-force longest paths above)."""
+    s = kkt_sequence(15, 20, 3, seed=7, steps=2, W=2.0)
+    A = s.csr(1)
+    p = oracle.min_degree(s.n, s.indptr, s.indices)
+    o = oracle.Oracle(s.n, s.indptr, s.indices, A.data, p)
+    lev, levu = o.F.levels()
+    y = np.random.default_rng(1).standard_normal(s.n)
+    ref, reft = o.F.solve(y), o.F.solve_t(y)
+    # the L (forward) and U (backward) chains have the same length on A + A^T
+    k = int(max(lev.max(), levu.max()))
+    for fn, r in ((o.F.jacobi_solve, ref), (o.F.jacobi_solve_t, reft)):
+        assert np.abs(fn(y, k) - r).max() <= 1e-9 * np.abs(r).max()
+        assert np.abs(fn(y, k - 3) - r).max() > 1e-7 * np.abs(r).max()
+
+
+def test_oracle_jacobi_closed_form_2x2():
+    """A = [[2, 1], [4, 5]] (natural order, no scaling): L = [[1, 0], [2, 1]],
+    U = [[2, 1], [0, 3]].  For y = (1, 1): w_0 = y, w_1 = (1, 1 - 2) = (1, -1);
+    z_0 = D^-1 w = (1/2, -1/3), z_1 = ((1 - (-1/3)) / 2, -1/3) = (2/3, -1/3),
+    the exact A^-1 y.  With 0 sweeps: (1/2, 1/3)."""
+    rp = np.array([0, 2, 4], np.int32)
+    ci = np.array([0, 1, 0, 1], np.int32)
+    o = oracle.Oracle(2, rp, ci, np.array([2.0, 1.0, 4.0, 5.0]), np.arange(2, dtype=np.int32), equil=False)
+    y = np.array([1.0, 1.0])
+    np.testing.assert_allclose(o.F.jacobi_solve(y, 1), [2 / 3, -1 / 3], rtol=1e-15)
+    np.testing.assert_allclose(o.F.jacobi_solve(y, 0), [1 / 2, 1 / 3], rtol=1e-15)
+    np.testing.assert_allclose(o.F.jacobi_solve_t(y, 1), np.linalg.solve(np.array([[2.0, 1], [4, 5]]).T, y),
+                               rtol=1e-15)
+
+
+def test_oracle_fgmres_with_jacobi_preconditioner_converges():
+    """FGMRES with a Jacobi-sweep preconditioner reaches omega <= 1e-14 on a
+    well-conditioned system (diagonally dominant, so the sweeps contract);
+    with 0 sweeps it needs more preconditioner applications than with 4."""
+    n = 200
+    rp, ci = random_sparse_pattern(n, 0.03, 61)
+    v = random_dd_values(rp, ci, 62, dominance=1.0)
+    b = np.random.default_rng(63).standard_normal(n)
+    o = oracle.Oracle(n, rp, ci, v, oracle.min_degree(n, rp, ci))
+    x4, it4, h4, ok4 = o.refine(b, mode="fgmres_jacobi", sweeps=4, max_it=60)
+    x0, it0, h0, ok0 = o.refine(b, mode="fgmres_jacobi", sweeps=0, max_it=60)
+    assert ok4 and ok0 and it4 < it0
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n)).toarray()
+    np.testing.assert_allclose(x4, np.linalg.solve(A, b), rtol=1e-9, atol=1e-12)
