@@ -117,6 +117,9 @@ typedef struct {
                                arithmetic).  Batched and queued calls use LU. */
     int jacobi_sweeps;      /* sweeps per triangular factor of KKT_REFINE_FGMRES_JACOBI
                                (default 8) */
+    const int *user_row_perm; /* NULL, or a host array of n rows: the context then
+                               factors Q A, whose row j is row user_row_perm[j] of A
+                               (copied during analysis; see kkt_analyze_values) */
 } kkt_options;
 
 typedef struct {
@@ -179,6 +182,32 @@ const char *kkt_last_error(void);
  */
 kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx,
                        const kkt_options *opt, kkt_ctx **out);
+
+/*
+ * Value-aware analysis (Sec. 5.2: MC64 matching before the fill-reducing
+ * ordering; Sec. 5.1: a pivot sequence chosen on the values of the first
+ * system).  A row permutation Q is computed from values_host (nnz float64 in
+ * CSR order): a perfect matching of the nonzeros that maximizes the product
+ * of the matched |a_ij| (the weighted bipartite matching MC64 solves), so Q A
+ * has a nonzero diagonal with the largest product; options.user_row_perm, when
+ * set, is used instead.  The pattern of Q A is then analyzed as by
+ * kkt_analyze, and the context factors Q A with diagonal pivots: KKT matrices
+ * without regularization, whose zero diagonal blocks give zero pivots in the
+ * pattern-only analysis, get nonzero ones.  Every call keeps the caller's
+ * numbering of A (values in A's CSR order, b, x, g, lambda, dA); the library
+ * applies Q at the boundary.  The exports describe Q A (kkt_export_row_perm
+ * gives Q).  Batched and queued calls are not available on such a context.
+ * The matching is recomputed only by a new analysis: when refinement returns
+ * KKT_ERR_NOT_CONVERGED the caller may analyze again on the current values
+ * (the paper's re-analysis policy, Sec. 5.1).  Errors: as kkt_analyze;
+ * KKT_ERR_PATTERN when A has no perfect matching (structurally singular).
+ */
+kkt_status kkt_analyze_values(int n, const int *row_ptr, const int *col_idx, const double *values_host,
+                              const kkt_options *opt, kkt_ctx **out);
+
+/* The row permutation of the context: row j of the factored matrix is row
+ * row_of_col[j] of A (the identity without one).  row_of_col: host, n ints. */
+kkt_status kkt_export_row_perm(const kkt_ctx *ctx, int *row_of_col);
 
 /* Release everything the context holds.  NULL is allowed. */
 void kkt_destroy(kkt_ctx *ctx);

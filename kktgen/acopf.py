@@ -142,6 +142,8 @@ class KKTSequence:
     W: float
     widen: bool
     asym: float = 0.0
+    reg: float = 1e-8      # regularization of the equality block (-reg I); 0: a zero
+                           # diagonal block, the KKT matrix is then not quasi-definite
     n_x: int = 0
     n: int = 0
     indptr: np.ndarray = field(default=None, repr=False)
@@ -240,7 +242,7 @@ class KKTSequence:
         wk = self.w(k)
         dx = 10.0 ** (wk * self._u)
         ds = 10.0 ** (wk * self._v)
-        dvals = np.concatenate([dsig + rowabs + dx, np.full(self.n_eq, -1e-8), -1.0 / ds])
+        dvals = np.concatenate([dsig + rowabs + dx, np.full(self.n_eq, -self.reg), -1.0 / ds])
         off = np.concatenate([h, h, je, je, ji, ji])
         if self._asym is not None:
             off = off * (1.0 + self.asym * self._asym)
@@ -260,9 +262,9 @@ class KKTSequence:
 
 
 def kkt_sequence(nb, nl, ng, seed, steps=10, W=6.0, widen=True, chords="local",
-                 asym=0.0) -> KKTSequence:
+                 asym=0.0, reg=1e-8) -> KKTSequence:
     grid = make_grid(nb, nl, ng, seed, chords=chords)
-    return KKTSequence(grid=grid, seed=seed, steps=steps, W=W, widen=widen, asym=asym)
+    return KKTSequence(grid=grid, seed=seed, steps=steps, W=W, widen=widen, asym=asym, reg=reg)
 
 
 def config_sequence(cfg: int, asym: float = 0.0, chords: str = "local") -> KKTSequence:

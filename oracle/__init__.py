@@ -114,6 +114,40 @@ def min_degree(n, indptr, indices):
     return perm
 
 
+def max_product_matching(n, indptr, indices, values):
+    """Row permutation q of a perfect matching of the nonzeros of A that
+    maximizes prod_j |a_{q[j], j}| (row j of Q A is row q[j] of A): the
+    weighted bipartite matching MC64 computes, which the paper's Ginkgo path
+    applies before the ordering (Sec. 5.2).  Plain definition: minimize
+    sum_j c(q[j], j) with c(i, j) = log max_k |a_kj| - log |a_ij| over the
+    nonzeros, solved by SciPy's min_weight_full_bipartite_matching as the step
+    (costs shifted by 1, which adds n to every perfect matching).  Raises
+    ValueError when A has no perfect matching."""
+    from scipy.sparse.csgraph import min_weight_full_bipartite_matching
+    A = sp.csr_matrix((np.array(values, dtype=np.float64), np.array(indices, dtype=np.int32),
+                       np.array(indptr, dtype=np.int32)), shape=(n, n))    # copies: the caller's arrays stay as they are
+    A.eliminate_zeros()
+    Ac = abs(A).tocsc()
+    colmax = np.zeros(n)
+    for j in range(n):
+        seg = Ac.data[Ac.indptr[j]:Ac.indptr[j + 1]]
+        colmax[j] = seg.max() if seg.size else 0.0
+    C = Ac.copy()
+    C.data = np.log(np.repeat(colmax, np.diff(Ac.indptr))) - np.log(Ac.data) + 1.0
+    r, c = min_weight_full_bipartite_matching(C.tocsr())
+    q = np.empty(n, dtype=np.int32)
+    q[c] = r
+    return q
+
+
+def row_permuted(n, indptr, indices, values, q):
+    """Q A as CSR (row j = row q[j] of A), values in the new row order."""
+    A = sp.csr_matrix((_f64(values), _i32(indices), _i32(indptr)), shape=(n, n))
+    B = A[np.asarray(q), :].tocsr()
+    B.sort_indices()
+    return _i32(B.indptr), _i32(B.indices), _f64(B.data)
+
+
 def equilibrate(n, indptr, values):
     """Power-of-two symmetric scaling s (reading: s_i = 2^-floor(floor(log2 r_i)/2),
     r_i = max_j |a_ij|); s_i = 1 for a zero or non-finite row."""

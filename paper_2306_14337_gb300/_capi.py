@@ -51,6 +51,7 @@ class Options(C.Structure):
         ("refactor_big_warps", C.c_int),
         ("symmetric", C.c_int),
         ("jacobi_sweeps", C.c_int),
+        ("user_row_perm", C.POINTER(C.c_int)),
     ]
 
 
@@ -133,6 +134,9 @@ SIGNATURES = {
     "kkt_probe_fma_tflops": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "kkt_inertia": (C.c_int, [_vp, _vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "kkt_solve_jacobi": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp]),
+    "kkt_analyze_values": (C.c_int, [C.c_int, _ip, _ip, C.POINTER(C.c_double), C.POINTER(Options),
+                                     C.POINTER(_vp)]),
+    "kkt_export_row_perm": (C.c_int, [_vp, _ip]),
 }
 
 _lib = None

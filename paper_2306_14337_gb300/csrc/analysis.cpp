@@ -13,6 +13,9 @@
 #include "analysis.h"
 
 #include <algorithm>
+#include <cmath>
+#include <limits>
+#include <queue>
 #include <cstring>
 #include <numeric>
 #include <atomic>
@@ -558,6 +561,124 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
             for (auto &t : th) t.join();
             if (bad) { err = "internal: update target outside the filled row"; return A_ERR_ARG; }
         }
+    }
+    return A_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Maximum-product matching (the weighted bipartite matching of Duff and
+// Koster's MC64, which the paper's Ginkgo path runs before AMD, Sec. 5.2).
+// Costs c(j,i) = log max_k |a_kj| - log |a_ij| >= 0 per column j over the
+// nonzero entries; a perfect matching of minimum total cost maximizes the
+// product of the matched |a_ij|.  Successive shortest augmenting paths with
+// dual potentials (Hungarian method): column potentials p, row potentials q,
+// reduced costs c - p - q >= 0 and 0 on matched edges; a greedy pass matches
+// every column it can on a zero reduced cost, then each free column finds the
+// nearest free row by Dijkstra over alternating paths and the potentials of
+// the nodes settled before it move by D - dist, which keeps every reduced
+// cost non-negative and makes the new path tight.
+int max_product_matching(int n, const int *rp, const int *ci, const double *val,
+                         std::vector<int> &row_of_col, std::string &err) {
+    // column-wise copy of the nonzero entries with their costs
+    std::vector<int> cp(n + 1, 0);
+    for (int r = 0; r < n; r++)
+        for (int p = rp[r]; p < rp[r + 1]; p++)
+            if (val[p] != 0.0 && std::isfinite(val[p])) cp[ci[p] + 1]++;
+    for (int j = 0; j < n; j++) cp[j + 1] += cp[j];
+    std::vector<int> crow(cp[n]);
+    std::vector<double> cost(cp[n]);
+    {
+        std::vector<int> fill(cp.begin(), cp.end() - 1);
+        for (int r = 0; r < n; r++)
+            for (int p = rp[r]; p < rp[r + 1]; p++)
+                if (val[p] != 0.0 && std::isfinite(val[p])) {
+                    const int j = ci[p];
+                    crow[fill[j]] = r;
+                    cost[fill[j]++] = std::log(std::fabs(val[p]));
+                }
+    }
+    for (int j = 0; j < n; j++) {
+        if (cp[j] == cp[j + 1]) { err = "matching: an empty column (structurally singular)"; return A_ERR_PATTERN; }
+        double m = -INFINITY;
+        for (int t = cp[j]; t < cp[j + 1]; t++) m = std::max(m, cost[t]);
+        for (int t = cp[j]; t < cp[j + 1]; t++) cost[t] = m - cost[t];
+    }
+    const double INF = std::numeric_limits<double>::infinity();
+    std::vector<double> pcol(n, 0.0), qrow(n, INF);
+    for (int j = 0; j < n; j++)
+        for (int t = cp[j]; t < cp[j + 1]; t++) qrow[crow[t]] = std::min(qrow[crow[t]], cost[t]);
+    for (int i = 0; i < n; i++)
+        if (!(qrow[i] < INF)) { err = "matching: an empty row (structurally singular)"; return A_ERR_PATTERN; }
+    row_of_col.assign(n, -1);
+    std::vector<int> col_of_row(n, -1);
+    for (int j = 0; j < n; j++)                       // greedy on tight edges
+        for (int t = cp[j]; t < cp[j + 1]; t++) {
+            const int i = crow[t];
+            if (col_of_row[i] < 0 && cost[t] - pcol[j] - qrow[i] <= 0.0) {
+                row_of_col[j] = i;
+                col_of_row[i] = j;
+                break;
+            }
+        }
+    std::vector<double> dist(n, INF);
+    std::vector<int> pred(n, -1);                     // row -> column it was reached from
+    std::vector<char> done(n, 0);
+    std::vector<int> touched, settled_rows, settled_cols;
+    typedef std::pair<double, int> QE;
+    for (int s = 0; s < n; s++) {
+        if (row_of_col[s] >= 0) continue;
+        std::priority_queue<QE, std::vector<QE>, std::greater<QE>> pq;
+        touched.clear();
+        settled_rows.clear();
+        settled_cols.clear();
+        auto relax = [&](int j, double dj) {
+            for (int t = cp[j]; t < cp[j + 1]; t++) {
+                const int i = crow[t];
+                if (done[i]) continue;
+                const double nd = dj + std::max(0.0, cost[t] - pcol[j] - qrow[i]);
+                if (nd < dist[i]) {
+                    if (!(dist[i] < INF)) touched.push_back(i);
+                    dist[i] = nd;
+                    pred[i] = j;
+                    pq.push(QE(nd, i));
+                }
+            }
+        };
+        std::vector<double> dcol_settled;
+        settled_cols.push_back(s);
+        dcol_settled.push_back(0.0);
+        relax(s, 0.0);
+        int t_row = -1;
+        double D = 0.0;
+        while (!pq.empty()) {
+            const QE e = pq.top();
+            pq.pop();
+            const int i = e.second;
+            if (done[i] || e.first > dist[i]) continue;
+            done[i] = 1;
+            settled_rows.push_back(i);
+            if (col_of_row[i] < 0) { t_row = i; D = dist[i]; break; }
+            const int j = col_of_row[i];
+            settled_cols.push_back(j);
+            dcol_settled.push_back(dist[i]);
+            relax(j, dist[i]);
+        }
+        if (t_row < 0) { err = "matching: no perfect matching (structurally singular)"; return A_ERR_PATTERN; }
+        // potentials of the nodes settled before the free row
+        for (size_t k = 0; k < settled_cols.size(); k++) pcol[settled_cols[k]] += D - dcol_settled[k];
+        for (int i : settled_rows)
+            if (i != t_row) qrow[i] -= D - dist[i];
+        // augment along the path back to s
+        int i = t_row;
+        while (i >= 0) {
+            const int j = pred[i];
+            const int prev = row_of_col[j];
+            row_of_col[j] = i;
+            col_of_row[i] = j;
+            i = (j == s) ? -1 : prev;
+        }
+        for (int r : touched) { dist[r] = INF; done[r] = 0; pred[r] = -1; }
     }
     return A_OK;
 }

@@ -66,6 +66,16 @@ void symmetric_graph(int n, const int *rp, const int *ci, std::vector<int> &grp,
 void amd_order(int n, const std::vector<int> &grp, const std::vector<int> &gci,
                std::vector<int> &perm);
 
+// Value-aware row permutation (Sec. 5.2: MC64 matching before the ordering):
+// row_of_col[j] = the row matched to column j in a perfect matching of the
+// nonzeros of A that maximizes the product of |a_{row_of_col[j], j}|, so the
+// row-permuted matrix Q A (row j of Q A = row row_of_col[j] of A) has a
+// nonzero diagonal with the largest possible product.  Returns A_OK, or
+// A_ERR_PATTERN (err set) when A has no perfect matching (structurally
+// singular).
+int max_product_matching(int n, const int *rp, const int *ci, const double *val,
+                         std::vector<int> &row_of_col, std::string &err);
+
 // Full analysis.  ordering: 0 AMD, 1 natural, 2 user (user_perm, new -> old).
 int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
             Analysis &out, std::string &err, long long map_budget_bytes = 0);

@@ -1969,6 +1969,19 @@ __global__ void k_perm_in(DevPattern P, const double *__restrict__ sp, const dou
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < P.n) c[i] = (T)(sp[i] * b[P.perm[i]]);
 }
+// row permutation Q of a value-aware context: out[k] = in[idx[k]] (gather) and
+// out[idx[k]] = in[k] (scatter), for values (nnz) and vectors (n)
+__global__ void k_gather(long long m, const int *__restrict__ idx, const double *__restrict__ in,
+                         double *__restrict__ out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) out[k] = in[idx[k]];
+}
+__global__ void k_scatter(long long m, const int *__restrict__ idx, const double *__restrict__ in,
+                          double *__restrict__ out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) out[idx[k]] = in[k];
+}
+
 template <typename T>
 __global__ void k_perm_out(DevPattern P, const double *__restrict__ sp, const T *__restrict__ z,
                            double *__restrict__ x, int accumulate) {
@@ -2281,6 +2294,16 @@ struct kkt_ctx {
     long long nnz_lu = 0;
     std::vector<int> at_rp, at_src;
     const double *values = nullptr;  // values of the current factorization (caller-owned)
+    // Value-aware row permutation (kkt_analyze_values / options.user_row_perm):
+    // the context factors Q A, row j of which is row q[j] of the caller's A.
+    // Values, right-hand sides and transposed solutions cross the boundary
+    // through gather/scatter kernels; all other work sees Q A.
+    bool rowperm = false;
+    std::vector<int> q, qmap;        // q[j]: row of A; qmap[k]: entry of A stored at entry k of Q A
+    int *d_q = nullptr, *d_qmap = nullptr;
+    double *d_qvals = nullptr;       // values of Q A (nnz)
+    double *d_qvec = nullptr;        // 2 n: Q b, and Q lambda
+    double *d_qdA = nullptr;         // gradient on the entries of Q A (nnz)
     bool factored = false;
     int last_iters = 0;
     double last_omega = -1.0;
@@ -2366,6 +2389,7 @@ void kkt_default_options(kkt_options *o) {
     o->refactor_big_warps = 0;
     o->symmetric = 0;
     o->jacobi_sweeps = 8;
+    o->user_row_perm = nullptr;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -2903,6 +2927,17 @@ static kkt_status upload(kkt_ctx *c) {
     c->rc.sched = c->d_sched;
     c->rc.cap = cap;
     c->rc.scratch = c->d_scratch;
+    if (c->rowperm) {
+        const size_t nnz = c->qmap.size();
+        CK(cudaMalloc(&c->d_q, (size_t)n * sizeof(int)));
+        CK(cudaMalloc(&c->d_qmap, nnz * sizeof(int)));
+        CK(cudaMalloc(&c->d_qvals, nnz * sizeof(double)));
+        CK(cudaMalloc(&c->d_qvec, 2 * (size_t)n * sizeof(double)));
+        CK(cudaMalloc(&c->d_qdA, nnz * sizeof(double)));
+        CK(cudaMemcpy(c->d_q, c->q.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_qmap, c->qmap.data(), nnz * sizeof(int), cudaMemcpyHostToDevice));
+        c->device_bytes += (size_t)n * 4 + nnz * 4 + nnz * 16 + 16 * (size_t)n;
+    }
     return KKT_OK;
 }
 
@@ -2910,6 +2945,11 @@ void kkt_destroy(kkt_ctx *c) {
     if (!c) return;
     if (!c->host_only) {
         DeviceGuard g(c->dev);
+        cudaFree(c->d_q);
+        cudaFree(c->d_qmap);
+        cudaFree(c->d_qvals);
+        cudaFree(c->d_qvec);
+        cudaFree(c->d_qdA);
         cudaFree(c->d_ints);
         cudaFree(c->d_lu);
         cudaFree(c->d_lut);
@@ -2942,8 +2982,10 @@ void kkt_destroy(kkt_ctx *c) {
     delete c;
 }
 
-kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_options *opt,
-                       kkt_ctx **out) {
+// Analysis of the pattern of A, or of Q A when a row permutation is given by
+// the options or computed from values_host (max-product matching).
+static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, const double *values_host,
+                              const kkt_options *opt, kkt_ctx **out) {
     if (!out) return KKT_ERR_ARG;
     *out = nullptr;
     std::unique_ptr<kkt_ctx> c(new (std::nothrow) kkt_ctx());
@@ -2973,7 +3015,46 @@ kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_
                     budget = 1LL << 30;
             }
         }
-        rc = analyze(n, row_ptr, col_idx, c->opt.ordering, c->opt.user_perm, c->an, err, budget);
+        const int *rp = row_ptr, *ci = col_idx;
+        std::vector<int> qa_rp, qa_ci;
+        if (c->opt.user_row_perm || values_host) {
+            if (!row_ptr || !col_idx || validate_pattern(n, row_ptr, col_idx) != A_OK) {
+                g_last_error = "malformed pattern";
+                return KKT_ERR_PATTERN;
+            }
+            std::vector<int> &q = c->q;
+            if (c->opt.user_row_perm) {
+                q.assign(c->opt.user_row_perm, c->opt.user_row_perm + n);
+                std::vector<char> seen(n, 0);
+                for (int j = 0; j < n; j++) {
+                    if (q[j] < 0 || q[j] >= n || seen[q[j]]) {
+                        g_last_error = "user_row_perm is not a permutation";
+                        return KKT_ERR_ARG;
+                    }
+                    seen[q[j]] = 1;
+                }
+            } else {
+                rc = max_product_matching(n, row_ptr, col_idx, values_host, q, err);
+                if (rc != A_OK) {
+                    g_last_error = err;
+                    return (kkt_status)rc;
+                }
+            }
+            // Q A: row j is row q[j] of A; qmap[k] = entry of A at entry k of Q A
+            qa_rp.assign(n + 1, 0);
+            for (int j = 0; j < n; j++) qa_rp[j + 1] = qa_rp[j] + row_ptr[q[j] + 1] - row_ptr[q[j]];
+            qa_ci.resize(qa_rp[n]);
+            c->qmap.resize(qa_rp[n]);
+            for (int j = 0; j < n; j++)
+                for (int t = 0; t < qa_rp[j + 1] - qa_rp[j]; t++) {
+                    qa_ci[qa_rp[j] + t] = col_idx[row_ptr[q[j]] + t];
+                    c->qmap[qa_rp[j] + t] = row_ptr[q[j]] + t;
+                }
+            c->rowperm = true;
+            rp = qa_rp.data();
+            ci = qa_ci.data();
+        }
+        rc = analyze(n, rp, ci, c->opt.ordering, c->opt.user_perm, c->an, err, budget);
     } catch (const std::bad_alloc &) {
         g_last_error = "host allocation failed during analysis";
         return KKT_ERR_ALLOC;
@@ -2983,6 +3064,7 @@ kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_
         return (kkt_status)rc;
     }
     c->opt.user_perm = nullptr;  // copied
+    c->opt.user_row_perm = nullptr;
     c->tau_rel = c->opt.pivot_tau_rel > 0 ? c->opt.pivot_tau_rel
                                           : (c->opt.factor_fp32 ? 0x1p-24 : 1e-14);
     c->dev = c->opt.device;
@@ -2997,6 +3079,24 @@ kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_
         }
     }
     *out = c.release();
+    return KKT_OK;
+}
+
+kkt_status kkt_analyze(int n, const int *row_ptr, const int *col_idx, const kkt_options *opt,
+                       kkt_ctx **out) {
+    return analyze_ctx(n, row_ptr, col_idx, nullptr, opt, out);
+}
+
+kkt_status kkt_analyze_values(int n, const int *row_ptr, const int *col_idx, const double *values_host,
+                              const kkt_options *opt, kkt_ctx **out) {
+    if (!values_host) return KKT_ERR_ARG;
+    return analyze_ctx(n, row_ptr, col_idx, values_host, opt, out);
+}
+
+kkt_status kkt_export_row_perm(const kkt_ctx *c, int *row_of_col) {
+    if (!c || !row_of_col) return KKT_ERR_ARG;
+    const int n = c->an.n;
+    for (int j = 0; j < n; j++) row_of_col[j] = c->rowperm ? c->q[j] : j;
     return KKT_OK;
 }
 
@@ -3088,11 +3188,29 @@ static kkt_status launch_solve_t(kkt_ctx *c, const double *g, double *lam, int a
     return KKT_OK;
 }
 
+// row permutation of a value-aware context: dst[j] = src[q[j]] (gather a
+// vector into Q's order) or dst[q[j]] = src[j] (scatter it back)
+static kkt_status q_vec(kkt_ctx *c, const double *src, double *dst, bool gather, cudaStream_t s) {
+    const int n = c->an.n;
+    if (gather) k_gather<<<blocks_for(n, 256), 256, 0, s>>>(n, c->d_q, src, dst);
+    else k_scatter<<<blocks_for(n, 256), 256, 0, s>>>(n, c->d_q, src, dst);
+    CK(cudaGetLastError());
+    c->launches++;
+    return KKT_OK;
+}
+
 kkt_status kkt_refactor(kkt_ctx *c, const double *values_dev, kkt_stream stream) {
     REQUIRE_DEVICE(c);
     if (!values_dev) return KKT_ERR_ARG;
     DeviceGuard g(c->dev);
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->rowperm) {                       // the values of Q A
+        const long long m = (long long)c->qmap.size();
+        k_gather<<<blocks_for(m, 256), 256, 0, s>>>(m, c->d_qmap, values_dev, c->d_qvals);
+        CK(cudaGetLastError());
+        c->launches++;
+        values_dev = c->d_qvals;
+    }
     c->values = values_dev;
     const int n = c->an.n;
     CK(cudaMemsetAsync(c->d_norms, 0, NM_WORDS * sizeof(unsigned long long), s));
@@ -3197,7 +3315,16 @@ kkt_status kkt_solve_jacobi(kkt_ctx *c, const double *b_dev, double *x_dev, int 
     if (!b_dev || !x_dev || b_dev == x_dev || sweeps < 0) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
     DeviceGuard g(c->dev);
-    return jacobi_any(c, b_dev, x_dev, 0, transpose ? 1 : 0, sweeps, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->rowperm) return jacobi_any(c, b_dev, x_dev, 0, transpose ? 1 : 0, sweeps, s);
+    kkt_status st;
+    if (!transpose) {                       // (Q A) x = Q b
+        if ((st = q_vec(c, b_dev, c->d_qvec, true, s))) return st;
+        return jacobi_any(c, c->d_qvec, x_dev, 0, 0, sweeps, s);
+    }
+    double *mu = c->d_qvec + c->an.n;       // (Q A)^T mu = g, lam = Q^T mu
+    if ((st = jacobi_any(c, b_dev, mu, 0, 1, sweeps, s))) return st;
+    return q_vec(c, mu, x_dev, false, s);
 }
 
 kkt_status kkt_solve(kkt_ctx *c, const double *b_dev, double *x_dev, kkt_stream stream) {
@@ -3205,7 +3332,13 @@ kkt_status kkt_solve(kkt_ctx *c, const double *b_dev, double *x_dev, kkt_stream 
     if (!b_dev || !x_dev || b_dev == x_dev) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
     DeviceGuard g(c->dev);
-    return solve_any(c, b_dev, x_dev, 0, 0, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->rowperm) {                       // (Q A) x = Q b: the columns, hence x, are not permuted
+        kkt_status st = q_vec(c, b_dev, c->d_qvec, true, s);
+        if (st) return st;
+        b_dev = c->d_qvec;
+    }
+    return solve_any(c, b_dev, x_dev, 0, 0, s);
 }
 
 kkt_status kkt_solve_transpose(kkt_ctx *c, const double *g_dev, double *lam_dev, kkt_stream stream) {
@@ -3213,7 +3346,12 @@ kkt_status kkt_solve_transpose(kkt_ctx *c, const double *g_dev, double *lam_dev,
     if (!g_dev || !lam_dev || g_dev == lam_dev) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
     DeviceGuard g(c->dev);
-    return solve_any(c, g_dev, lam_dev, 0, 1, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->rowperm) return solve_any(c, g_dev, lam_dev, 0, 1, s);
+    double *mu = c->d_qvec + c->an.n;       // A^T lam = g  <=>  (Q A)^T (Q lam) = g
+    kkt_status st = solve_any(c, g_dev, mu, 0, 1, s);
+    if (st) return st;
+    return q_vec(c, mu, lam_dev, false, s);
 }
 
 // residual + norms; returns omega on the host (synchronises the stream)
@@ -3416,7 +3554,13 @@ kkt_status kkt_refine(kkt_ctx *c, const double *b_dev, double *x_dev, double tol
     if (!b_dev || !x_dev || b_dev == x_dev) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
     DeviceGuard g(c->dev);
-    return refine_any(c, b_dev, x_dev, tol, max_it, info, 0, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->rowperm) {                       // the residual of Q A x = Q b has the norms of A x = b
+        kkt_status st = q_vec(c, b_dev, c->d_qvec, true, s);
+        if (st) return st;
+        b_dev = c->d_qvec;
+    }
+    return refine_any(c, b_dev, x_dev, tol, max_it, info, 0, s);
 }
 
 kkt_status kkt_refine_transpose(kkt_ctx *c, const double *g_dev, double *lam_dev, double tol,
@@ -3425,7 +3569,15 @@ kkt_status kkt_refine_transpose(kkt_ctx *c, const double *g_dev, double *lam_dev
     if (!g_dev || !lam_dev || g_dev == lam_dev) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
     DeviceGuard g(c->dev);
-    return refine_any(c, g_dev, lam_dev, tol, max_it, info, 1, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->rowperm) return refine_any(c, g_dev, lam_dev, tol, max_it, info, 1, s);
+    double *mu = c->d_qvec + c->an.n;       // refine mu = Q lam on (Q A)^T mu = g
+    kkt_status st = q_vec(c, lam_dev, mu, true, s);
+    if (st) return st;
+    const kkt_status r = refine_any(c, g_dev, mu, tol, max_it, info, 1, s);
+    if (r == KKT_ERR_CUDA) return r;
+    st = q_vec(c, mu, lam_dev, false, s);
+    return st ? st : r;
 }
 
 // ---------------------------------------------------------------------------
@@ -3436,6 +3588,10 @@ static void ensure_view(const kkt_ctx *c);
 #define REQUIRE_BATCH(c, B)                                                                  \
     do {                                                                                     \
         REQUIRE_DEVICE(c);                                                                   \
+        if ((c)->rowperm) {                                                                  \
+            g_last_error = "batched calls do not support a row permutation";                 \
+            return KKT_ERR_STATE;                                                            \
+        }                                                                                    \
         if ((B) < 1 || (B) > (c)->bcap) {                                                    \
             g_last_error = "batch size outside 1..max_batch (set max_batch at analysis)";    \
             return KKT_ERR_ARG;                                                              \
@@ -3707,6 +3863,7 @@ kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
     for (int k = 0; k < m; k++) {
         kkt_ctx *c = ctxs[k];
         if (!c || c->host_only) { g_last_error = "queue needs device contexts"; return KKT_ERR_ARG; }
+        if (c->rowperm) { g_last_error = "queue contexts cannot carry a row permutation"; return KKT_ERR_STATE; }
         if (k && (c->dev != ctxs[0]->dev || c->opt.factor_fp32 != ctxs[0]->opt.factor_fp32)) {
             g_last_error = "queue contexts must share the device and the factor precision";
             return KKT_ERR_ARG;
@@ -4023,10 +4180,23 @@ kkt_status kkt_adjoint_gather(kkt_ctx *c, const double *lam_dev, const double *x
     REQUIRE_DEVICE(c);
     if (!lam_dev || !x_dev || !dA_dev) return KKT_ERR_ARG;
     DeviceGuard g(c->dev);
+    cudaStream_t s = (cudaStream_t)stream;
     const long long m = c->P.nnz_a;
-    k_adjoint<<<blocks_for(m, 256), 256, 0, (cudaStream_t)stream>>>(c->P, lam_dev, x_dev, dA_dev);
+    if (!c->rowperm) {
+        k_adjoint<<<blocks_for(m, 256), 256, 0, s>>>(c->P, lam_dev, x_dev, dA_dev);
+        CK(cudaGetLastError());
+        c->launches++;
+        return KKT_OK;
+    }
+    // entry k of Q A is entry qmap[k] of A, in row q[j] of A: dA = -lam[q[j]] x[col]
+    double *mu = c->d_qvec + c->an.n;
+    kkt_status st = q_vec(c, lam_dev, mu, true, s);
+    if (st) return st;
+    k_adjoint<<<blocks_for(m, 256), 256, 0, s>>>(c->P, mu, x_dev, c->d_qdA);
     CK(cudaGetLastError());
-    c->launches++;
+    k_scatter<<<blocks_for(m, 256), 256, 0, s>>>(m, c->d_qmap, c->d_qdA, dA_dev);
+    CK(cudaGetLastError());
+    c->launches += 2;
     return KKT_OK;
 }
 

@@ -39,13 +39,18 @@ class KKTSolver:
     indptr, indices: CSR pattern (host arrays, sorted and unique per row).
     device: CUDA device index, or None for a host-only analysis (no CUDA call;
     only ``stats`` and ``export_symbolic`` work).
+    values: host values (CSR order) for a value-aware analysis
+    (kkt_analyze_values: a max-product matching row permutation before the
+    ordering); row_perm: a row permutation to use instead (row j of the
+    factored matrix is row row_perm[j] of A).
     """
 
     def __init__(self, n, indptr, indices, *, fp32=False, equilibrate=True, ordering="amd",
                  perm=None, refine_mode="classic", tol=1e-14, max_refine=20,
                  pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
                  solve_ctas=0, update_map_budget=0, trace=False, max_batch=1, unpublished_row=-1,
-                 poll_ns_max=0, refactor_big_warps=0, symmetric=False, jacobi_sweeps=8, device=0):
+                 poll_ns_max=0, refactor_big_warps=0, symmetric=False, jacobi_sweeps=8, values=None,
+                 row_perm=None, device=0):
         self._lib = _capi.load()
         self.n = int(n)
         self._rp = _i32(indptr)
@@ -76,15 +81,28 @@ class KKTSolver:
         opt.refactor_big_warps = int(refactor_big_warps)
         opt.symmetric = int(bool(symmetric))
         opt.jacobi_sweeps = int(jacobi_sweeps)
+        self._row_perm = None
+        if row_perm is not None:
+            self._row_perm = _i32(row_perm)
+            opt.user_row_perm = self._row_perm.ctypes.data_as(C.POINTER(C.c_int))
         self.device = None if device is None else torch.device("cuda", int(device)) if not isinstance(
             device, torch.device) else device
         opt.device = -1 if self.device is None else (self.device.index or 0)
         self.fp32 = bool(fp32)
+        self._opt = opt
         h = C.c_void_p()
-        st = self._lib.kkt_analyze(self.n, self._rp.ctypes.data_as(C.POINTER(C.c_int)),
-                                   self._ci.ctypes.data_as(C.POINTER(C.c_int)), C.byref(opt),
-                                   C.byref(h))
-        check(st, "kkt_analyze")
+        if values is not None:
+            vals = np.ascontiguousarray(np.asarray(values), dtype=np.float64)
+            st = self._lib.kkt_analyze_values(self.n, self._rp.ctypes.data_as(C.POINTER(C.c_int)),
+                                              self._ci.ctypes.data_as(C.POINTER(C.c_int)),
+                                              vals.ctypes.data_as(C.POINTER(C.c_double)), C.byref(opt),
+                                              C.byref(h))
+            check(st, "kkt_analyze_values")
+        else:
+            st = self._lib.kkt_analyze(self.n, self._rp.ctypes.data_as(C.POINTER(C.c_int)),
+                                       self._ci.ctypes.data_as(C.POINTER(C.c_int)), C.byref(opt),
+                                       C.byref(h))
+            check(st, "kkt_analyze")
         self._h = h
         self._values = None
         self.version = 0           # bumped by every refactor
@@ -113,6 +131,51 @@ class KKTSolver:
         check(self._lib.kkt_export_symbolic(self._h, P(perm), P(rp), P(ci), P(lev), P(levu)),
               "kkt_export_symbolic")
         return dict(perm=perm, lu_rp=rp, lu_ci=ci, level=lev, level_u=levu)
+
+    def export_row_perm(self) -> np.ndarray:
+        """Row permutation of the factored matrix (identity without one)."""
+        q = np.zeros(self.n, np.int32)
+        check(self._lib.kkt_export_row_perm(self._h, q.ctypes.data_as(C.POINTER(C.c_int))),
+              "kkt_export_row_perm")
+        return q
+
+    def reanalyze(self, values):
+        """Analyze again with the given host values (kkt_analyze_values: a new
+        max-product matching and ordering), replacing this context; the other
+        options are kept, except that a caller-given ordering (meaningful for
+        A, not for the new Q A) is replaced by the minimum-degree one.  The
+        paper's policy when refinement fails with the fixed pivot sequence
+        (Sec. 5.1)."""
+        vals = np.ascontiguousarray(np.asarray(values), dtype=np.float64)
+        h = C.c_void_p()
+        self._opt.user_row_perm = C.POINTER(C.c_int)()
+        if self._opt.ordering == _capi.ORDER_USER:
+            self._opt.ordering = _capi.ORDER_AMD
+            self._opt.user_perm = C.POINTER(C.c_int)()
+        check(self._lib.kkt_analyze_values(self.n, self._rp.ctypes.data_as(C.POINTER(C.c_int)),
+                                           self._ci.ctypes.data_as(C.POINTER(C.c_int)),
+                                           vals.ctypes.data_as(C.POINTER(C.c_double)), C.byref(self._opt),
+                                           C.byref(h)), "kkt_analyze_values")
+        self._lib.kkt_destroy(self._h)
+        self._h = h
+        self._values = None
+
+    def solve_robust(self, values: torch.Tensor, b: torch.Tensor, tol=1e-14, max_it=20, stream=None) -> dict:
+        """Refactor, solve and refine; if refinement misses tol (or meets a
+        non-finite value), analyze again on these values (value-aware) and
+        repeat once.  Returns the refinement record with "x" and "reanalyzed"."""
+        self.refactor(values, stream)
+        x = self.solve(b, stream=stream)
+        info = self.refine(b, x, tol, max_it, stream)
+        info["reanalyzed"] = False
+        if not info["converged"]:
+            self.reanalyze(values.detach().cpu().numpy())
+            self.refactor(values, stream)
+            x = self.solve(b, stream=stream)
+            info = self.refine(b, x, tol, max_it, stream)
+            info["reanalyzed"] = True
+        info["x"] = x
+        return info
 
     def export_factors(self, stream=None) -> torch.Tensor:
         out = torch.empty(self.stats()["nnz_lu"], dtype=torch.float64, device=self.device)

@@ -626,3 +626,45 @@ def test_oracle_fgmres_with_jacobi_preconditioner_converges():
     assert ok4 and ok0 and it4 < it0
     A = sp.csr_matrix((v, ci, rp), shape=(n, n)).toarray()
     np.testing.assert_allclose(x4, np.linalg.solve(A, b), rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_oracle_matching_is_the_max_product_permutation(seed):
+    """Brute force over all n! row permutations (n = 6): the oracle's matching
+    attains the largest |product| of a diagonal of Q A."""
+    import itertools
+    n = 6
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.5)
+    M[np.arange(n), rng.permutation(n)] = 1.0 + rng.random(n)     # a perfect matching exists
+    A = sp.csr_matrix(M)
+    q = oracle.max_product_matching(n, A.indptr, A.indices, A.data)
+    best = max(abs(np.prod([M[p[j], j] for j in range(n)])) for p in itertools.permutations(range(n)))
+    got = abs(np.prod([M[q[j], j] for j in range(n)]))
+    assert got == pytest.approx(best, rel=1e-12) and best > 0
+    rp, ci, v = oracle.row_permuted(n, A.indptr, A.indices, A.data, q)
+    assert np.array_equal(sp.csr_matrix((v, ci, rp), shape=(n, n)).toarray(), M[q, :])
+
+
+def test_library_matching_reaches_the_oracle_optimum():
+    """The library's own matching (kkt_analyze_values, host-only analysis)
+    attains the same optimal sum of log |a| as the oracle's on random sparse
+    matrices and on a KKT matrix with a zero equality block (no -1e-8
+    regularization), and gives Q A a nonzero diagonal."""
+    from paper_2306_14337_gb300 import KKTSolver
+    cases = []
+    for seed in (5, 6):
+        rp, ci = random_sparse_pattern(300, 0.02, seed)
+        cases.append((300, rp, ci, np.random.default_rng(seed).standard_normal(ci.size)))
+    s = kkt_sequence(60, 78, 12, seed=3, steps=2, W=4.0, reg=0.0)
+    cases.append((s.n, s.indptr, s.indices, s.values(1)))
+    for n, rp, ci, v in cases:
+        S = KKTSolver(n, rp, ci, values=v, device=None)
+        q = S.export_row_perm()
+        rp0, ci0, v0 = rp.copy(), ci.copy(), v.copy()
+        qo = oracle.max_product_matching(n, rp, ci, v)
+        assert np.array_equal(rp, rp0) and np.array_equal(ci, ci0) and np.array_equal(v, v0)
+        A = sp.csr_matrix((v, ci, rp), shape=(n, n)).toarray()
+        dl, do = A[q, np.arange(n)], A[qo, np.arange(n)]
+        assert np.all(dl != 0) and sorted(q.tolist()) == list(range(n))
+        assert np.sum(np.log(np.abs(dl))) == pytest.approx(np.sum(np.log(np.abs(do))), rel=1e-10, abs=1e-9)
