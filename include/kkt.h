@@ -303,6 +303,23 @@ kkt_status kkt_get_stats(const kkt_ctx *ctx, kkt_stats *stats);
 kkt_status kkt_export_symbolic(const kkt_ctx *ctx, int *perm, int *lu_row_ptr,
                                int *lu_col_idx, int *level, int *level_u);
 
+/*
+ * Checkpoint and resume of the analysis (Sec. 4 and Sec. 5.2: one symbolic
+ * analysis serves every later system; a saved one lets a new run skip it).
+ * kkt_save_analysis writes a self-contained image of everything the analysis
+ * computed -- ordering, fill pattern, levels, maps, solve tasks, and the row
+ * permutation of a value-aware context -- ending in a 64-bit checksum: with
+ * buf NULL it only stores the size needed in *size; otherwise cap must be at
+ * least that size.  kkt_load_analysis creates a context from such an image
+ * with the given options (their ordering, user_perm and user_row_perm are
+ * ignored: the image fixes them; the update maps are those of the image) and
+ * allocates and uploads as kkt_analyze does.  An image whose checksum,
+ * version or array sizes do not match returns KKT_ERR_ARG.  The image must
+ * come from kkt_save_analysis of this library version.
+ */
+kkt_status kkt_save_analysis(const kkt_ctx *ctx, void *buf, size_t cap, size_t *size);
+kkt_status kkt_load_analysis(const void *buf, size_t size, const kkt_options *opt, kkt_ctx **out);
+
 /* Copy the current factor values (float64, in the lu_col_idx order of
  * kkt_export_symbolic; L strictly below the diagonal, U on and above it) to
  * out_dev (nnz_lu float64). */

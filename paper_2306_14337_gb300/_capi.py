@@ -137,6 +137,8 @@ SIGNATURES = {
     "kkt_analyze_values": (C.c_int, [C.c_int, _ip, _ip, C.POINTER(C.c_double), C.POINTER(Options),
                                      C.POINTER(_vp)]),
     "kkt_export_row_perm": (C.c_int, [_vp, _ip]),
+    "kkt_save_analysis": (C.c_int, [_vp, _vp, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "kkt_load_analysis": (C.c_int, [_vp, C.c_size_t, C.POINTER(Options), C.POINTER(_vp)]),
 }
 
 _lib = None

@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.returncode:
             raise RuntimeError(f"compile failed: {c[0]} ({p.returncode})")
     tmp = LIB + f".{tag}.tmp"
-    link = [nvcc, "-shared", *ARCH, "-o", tmp, o_host, o_dev, o_na, o_pr, "-lpthread"]
+    link = [nvcc, "-shared", *ARCH, "-o", tmp, o_host, o_dev, o_na, o_pr, "-lpthread", "-ldl"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if verbose or r.returncode:
         sys.stderr.write(" ".join(link) + "\n" + r.stdout)

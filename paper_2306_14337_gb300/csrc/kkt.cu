@@ -40,6 +40,8 @@
 #include <map>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kkt.h"
 #include "analysis.h"
 #include "kernels.cuh"
@@ -2328,6 +2330,13 @@ static kkt_status cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 namespace {
+// A named range around every entry point for profilers (NVTX; costs a few ns
+// when no profiler is attached).
+struct ApiRange {
+    explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+};
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
@@ -2986,6 +2995,7 @@ void kkt_destroy(kkt_ctx *c) {
 // the options or computed from values_host (max-product matching).
 static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, const double *values_host,
                               const kkt_options *opt, kkt_ctx **out) {
+    ApiRange nvtx_range(values_host ? "kkt_analyze_values" : "kkt_analyze");
     if (!out) return KKT_ERR_ARG;
     *out = nullptr;
     std::unique_ptr<kkt_ctx> c(new (std::nothrow) kkt_ctx());
@@ -3200,6 +3210,7 @@ static kkt_status q_vec(kkt_ctx *c, const double *src, double *dst, bool gather,
 }
 
 kkt_status kkt_refactor(kkt_ctx *c, const double *values_dev, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_refactor");
     REQUIRE_DEVICE(c);
     if (!values_dev) return KKT_ERR_ARG;
     DeviceGuard g(c->dev);
@@ -3311,6 +3322,7 @@ static kkt_status precond_any(kkt_ctx *c, const double *b, double *x, int transp
 
 kkt_status kkt_solve_jacobi(kkt_ctx *c, const double *b_dev, double *x_dev, int sweeps, int transpose,
                             kkt_stream stream) {
+    ApiRange nvtx_range("kkt_solve_jacobi");
     REQUIRE_DEVICE(c);
     if (!b_dev || !x_dev || b_dev == x_dev || sweeps < 0) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
@@ -3328,6 +3340,7 @@ kkt_status kkt_solve_jacobi(kkt_ctx *c, const double *b_dev, double *x_dev, int 
 }
 
 kkt_status kkt_solve(kkt_ctx *c, const double *b_dev, double *x_dev, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_solve");
     REQUIRE_DEVICE(c);
     if (!b_dev || !x_dev || b_dev == x_dev) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
@@ -3342,6 +3355,7 @@ kkt_status kkt_solve(kkt_ctx *c, const double *b_dev, double *x_dev, kkt_stream 
 }
 
 kkt_status kkt_solve_transpose(kkt_ctx *c, const double *g_dev, double *lam_dev, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_solve_transpose");
     REQUIRE_DEVICE(c);
     if (!g_dev || !lam_dev || g_dev == lam_dev) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
@@ -3550,6 +3564,7 @@ static kkt_status refine_any(kkt_ctx *c, const double *b, double *x, double tol,
 
 kkt_status kkt_refine(kkt_ctx *c, const double *b_dev, double *x_dev, double tol, int max_it,
                       kkt_refine_info *info, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_refine");
     REQUIRE_DEVICE(c);
     if (!b_dev || !x_dev || b_dev == x_dev) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
@@ -3565,6 +3580,7 @@ kkt_status kkt_refine(kkt_ctx *c, const double *b_dev, double *x_dev, double tol
 
 kkt_status kkt_refine_transpose(kkt_ctx *c, const double *g_dev, double *lam_dev, double tol,
                                 int max_it, kkt_refine_info *info, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_refine_transpose");
     REQUIRE_DEVICE(c);
     if (!g_dev || !lam_dev || g_dev == lam_dev) return KKT_ERR_ARG;
     if (!c->factored) return KKT_ERR_STATE;
@@ -3611,6 +3627,7 @@ template <typename T> static kkt_status launch_brefactor(kkt_ctx *c, int B, cuda
 }
 
 kkt_status kkt_batch_refactor(kkt_ctx *c, int B, const double *values_dev, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_batch_refactor");
     REQUIRE_BATCH(c, B);
     if (!values_dev) return KKT_ERR_ARG;
     DeviceGuard g(c->dev);
@@ -3664,6 +3681,7 @@ static kkt_status bsolve_any(kkt_ctx *c, int B, const double *b, double *x, int 
 }
 
 kkt_status kkt_batch_solve(kkt_ctx *c, int B, const double *b_dev, double *x_dev, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_batch_solve");
     REQUIRE_BATCH(c, B);
     if (!b_dev || !x_dev || b_dev == x_dev) return KKT_ERR_ARG;
     if (c->b_factored != B) return KKT_ERR_STATE;
@@ -3673,6 +3691,7 @@ kkt_status kkt_batch_solve(kkt_ctx *c, int B, const double *b_dev, double *x_dev
 
 kkt_status kkt_batch_solve_transpose(kkt_ctx *c, int B, const double *g_dev, double *lam_dev,
                                      kkt_stream stream) {
+    ApiRange nvtx_range("kkt_batch_solve_transpose");
     REQUIRE_BATCH(c, B);
     if (!g_dev || !lam_dev || g_dev == lam_dev) return KKT_ERR_ARG;
     if (c->b_factored != B) return KKT_ERR_STATE;
@@ -3738,6 +3757,7 @@ static kkt_status brefine_any(kkt_ctx *c, int B, const double *b, double *x, dou
 
 kkt_status kkt_batch_refine(kkt_ctx *c, int B, const double *b_dev, double *x_dev, double tol, int max_it,
                             double *omega_host, int *iters, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_batch_refine");
     REQUIRE_BATCH(c, B);
     if (!b_dev || !x_dev || b_dev == x_dev) return KKT_ERR_ARG;
     if (c->b_factored != B) return KKT_ERR_STATE;
@@ -3747,6 +3767,7 @@ kkt_status kkt_batch_refine(kkt_ctx *c, int B, const double *b_dev, double *x_de
 
 kkt_status kkt_batch_refine_transpose(kkt_ctx *c, int B, const double *g_dev, double *lam_dev, double tol,
                                       int max_it, double *omega_host, int *iters, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_batch_refine_transpose");
     REQUIRE_BATCH(c, B);
     if (!g_dev || !lam_dev || g_dev == lam_dev) return KKT_ERR_ARG;
     if (c->b_factored != B) return KKT_ERR_STATE;
@@ -4071,6 +4092,7 @@ static kkt_status q_record(kkt_queue *q, int n_refine, double *omega_dev, cudaSt
 
 kkt_status kkt_queue_run(kkt_queue *q, const double *const *values, const double *const *b, double *const *x,
                          int n_refine, double *omega_dev, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_queue_run");
     if (!q || !values || !b || !x || n_refine < 0) return KKT_ERR_ARG;
     DeviceGuard g(q->dev);
     cudaStream_t s = (cudaStream_t)stream;
@@ -4118,6 +4140,7 @@ kkt_status kkt_queue_run(kkt_queue *q, const double *const *values, const double
 }
 
 kkt_status kkt_queue_solve_transpose(kkt_queue *q, const double *const *g_, double *const *lam, kkt_stream stream) {
+    ApiRange nvtx_range("kkt_queue_solve_transpose");
     if (!q || !g_ || !lam) return KKT_ERR_ARG;
     DeviceGuard g(q->dev);
     cudaStream_t s = (cudaStream_t)stream;
@@ -4177,6 +4200,7 @@ kkt_status kkt_queue_status_sync(kkt_queue *q, kkt_stream stream, int *n_perturb
 
 kkt_status kkt_adjoint_gather(kkt_ctx *c, const double *lam_dev, const double *x_dev, double *dA_dev,
                               kkt_stream stream) {
+    ApiRange nvtx_range("kkt_adjoint_gather");
     REQUIRE_DEVICE(c);
     if (!lam_dev || !x_dev || !dA_dev) return KKT_ERR_ARG;
     DeviceGuard g(c->dev);
@@ -4289,6 +4313,147 @@ kkt_status kkt_get_stats(const kkt_ctx *c, kkt_stats *o) {
     o->update_map_entries = (long long)a.upd_map.size();
     o->n_tasks = (int)a.task_lo.size();
     o->max_task = a.max_task;
+    return KKT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint of the analysis: a flat image of everything kkt_analyze computed
+// (and the row permutation of a value-aware context), so a later run can skip
+// the host analysis.  Layout: "KKTA", version, then for every array its
+// length (int64) and contents, then the scalars, then a 64-bit FNV-1a checksum
+// of all preceding bytes.
+namespace {
+constexpr unsigned kImgMagic = 0x41544b4bu;   // "KKTA"
+constexpr unsigned kImgVersion = 1;
+
+struct ImgWriter {
+    std::vector<unsigned char> out;
+    void raw(const void *p, size_t b) {
+        const unsigned char *q = static_cast<const unsigned char *>(p);
+        out.insert(out.end(), q, q + b);
+    }
+    template <typename T> void val(T v) { raw(&v, sizeof(v)); }
+    template <typename T> void vec(const std::vector<T> &v) {
+        val<long long>((long long)v.size());
+        if (!v.empty()) raw(v.data(), v.size() * sizeof(T));
+    }
+};
+struct ImgReader {
+    const unsigned char *p;
+    size_t left;
+    bool ok = true;
+    void raw(void *d, size_t b) {
+        if (!ok || b > left) { ok = false; return; }
+        std::memcpy(d, p, b);
+        p += b;
+        left -= b;
+    }
+    template <typename T> T val() { T v{}; raw(&v, sizeof(v)); return v; }
+    template <typename T> void vec(std::vector<T> &v, long long expect = -1) {
+        const long long m = val<long long>();
+        if (!ok || m < 0 || (expect >= 0 && m != expect) || (unsigned long long)m * sizeof(T) > left) {
+            ok = false;
+            return;
+        }
+        v.resize((size_t)m);
+        if (m) raw(v.data(), (size_t)m * sizeof(T));
+    }
+};
+unsigned long long fnv1a(const unsigned char *p, size_t b) {
+    unsigned long long h = 1469598103934665603ull;
+    for (size_t i = 0; i < b; i++) { h ^= p[i]; h *= 1099511628211ull; }
+    return h;
+}
+}  // namespace
+
+kkt_status kkt_save_analysis(const kkt_ctx *c, void *buf, size_t cap, size_t *size) {
+    if (!c || !size) return KKT_ERR_ARG;
+    const Analysis &a = c->an;
+    ImgWriter w;
+    w.val(kImgMagic);
+    w.val(kImgVersion);
+    w.val(a.n);
+    w.vec(a.a_rp); w.vec(a.a_ci); w.vec(a.a_row); w.vec(a.perm); w.vec(a.iperm);
+    w.vec(a.view_perm); w.vec(a.view_of); w.vec(a.internal_of); w.vec(a.parent);
+    w.vec(a.lu_rp); w.vec(a.lu_ci); w.vec(a.diag); w.vec(a.src); w.vec(a.tpos);
+    w.vec(a.level); w.vec(a.level_u); w.vec(a.order_f); w.vec(a.order_b);
+    w.vec(a.task_lo); w.vec(a.task_hi); w.vec(a.upd_off); w.vec(a.upd_map);
+    w.val(a.n_levels); w.val(a.n_levels_u); w.val(a.nnz_sym); w.val(a.max_row); w.val(a.flops);
+    w.val(a.max_task);
+    w.val<int>(c->rowperm ? 1 : 0);
+    w.vec(c->q); w.vec(c->qmap);
+    w.val(fnv1a(w.out.data(), w.out.size()));
+    *size = w.out.size();
+    if (!buf) return KKT_OK;
+    if (cap < w.out.size()) { g_last_error = "kkt_save_analysis: buffer too small"; return KKT_ERR_ARG; }
+    std::memcpy(buf, w.out.data(), w.out.size());
+    return KKT_OK;
+}
+
+kkt_status kkt_load_analysis(const void *buf, size_t size, const kkt_options *opt, kkt_ctx **out) {
+    if (!buf || !out || size < 8 + 16) return KKT_ERR_ARG;
+    *out = nullptr;
+    ApiRange nvtx_range("kkt_load_analysis");
+    const unsigned char *b = static_cast<const unsigned char *>(buf);
+    unsigned long long sum = 0;
+    std::memcpy(&sum, b + size - 8, 8);
+    if (fnv1a(b, size - 8) != sum) { g_last_error = "analysis image: checksum mismatch"; return KKT_ERR_ARG; }
+    std::unique_ptr<kkt_ctx> c(new (std::nothrow) kkt_ctx());
+    if (!c) return KKT_ERR_ALLOC;
+    if (opt) c->opt = *opt; else kkt_default_options(&c->opt);
+    Analysis &a = c->an;
+    try {
+        ImgReader r{b, size - 8};
+        if (r.val<unsigned>() != kImgMagic || r.val<unsigned>() != kImgVersion) {
+            g_last_error = "analysis image: not a kkt analysis of this version";
+            return KKT_ERR_ARG;
+        }
+        a.n = r.val<int>();
+        const long long n = a.n;
+        if (!r.ok || n <= 0) { g_last_error = "analysis image: bad size"; return KKT_ERR_ARG; }
+        r.vec(a.a_rp, n + 1); r.vec(a.a_ci); r.vec(a.a_row); r.vec(a.perm, n); r.vec(a.iperm, n);
+        r.vec(a.view_perm, n); r.vec(a.view_of, n); r.vec(a.internal_of, n); r.vec(a.parent, n);
+        r.vec(a.lu_rp, n + 1); r.vec(a.lu_ci); r.vec(a.diag, n); r.vec(a.src); r.vec(a.tpos);
+        r.vec(a.level, n); r.vec(a.level_u, n); r.vec(a.order_f, n); r.vec(a.order_b, n);
+        r.vec(a.task_lo); r.vec(a.task_hi); r.vec(a.upd_off); r.vec(a.upd_map);
+        a.n_levels = r.val<int>(); a.n_levels_u = r.val<int>(); a.nnz_sym = r.val<long long>();
+        a.max_row = r.val<int>(); a.flops = r.val<double>(); a.max_task = r.val<int>();
+        c->rowperm = r.val<int>() != 0;
+        r.vec(c->q); r.vec(c->qmap);
+        // the sizes the kernels rely on
+        const long long nlu = (long long)a.lu_ci.size(), nna = (long long)a.a_ci.size();
+        bool ok = r.ok && r.left == 0 && a.lu_rp[0] == 0 && a.lu_rp[n] == nlu && a.a_rp[0] == 0 &&
+                  a.a_rp[n] == nna && (long long)a.a_row.size() == nna && (long long)a.src.size() == nlu &&
+                  (long long)a.tpos.size() == nlu && a.task_lo.size() == a.task_hi.size() &&
+                  (a.upd_off.empty() || (long long)a.upd_off.size() == nlu) &&
+                  (!c->rowperm || ((long long)c->q.size() == n && (long long)c->qmap.size() == nna));
+        for (long long i = 0; ok && i < n; i++)
+            ok = a.lu_rp[i] <= a.lu_rp[i + 1] && a.a_rp[i] <= a.a_rp[i + 1] && a.diag[i] >= a.lu_rp[i] &&
+                 a.diag[i] < a.lu_rp[i + 1] && a.perm[i] >= 0 && a.perm[i] < n && a.order_f[i] >= 0 &&
+                 a.order_f[i] < n && a.order_b[i] >= 0 && a.order_b[i] < n;
+        for (long long k = 0; ok && k < nlu; k++)
+            ok = a.lu_ci[k] >= 0 && a.lu_ci[k] < n && a.src[k] >= -1 && a.src[k] < nna && a.tpos[k] >= 0 &&
+                 a.tpos[k] < nlu && (a.upd_off.empty() || a.upd_off[k] <= a.upd_map.size());
+        if (!ok) { g_last_error = "analysis image: inconsistent arrays"; return KKT_ERR_ARG; }
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed while loading an analysis";
+        return KKT_ERR_ALLOC;
+    }
+    c->opt.user_perm = nullptr;
+    c->opt.user_row_perm = nullptr;
+    c->tau_rel = c->opt.pivot_tau_rel > 0 ? c->opt.pivot_tau_rel : (c->opt.factor_fp32 ? 0x1p-24 : 1e-14);
+    c->dev = c->opt.device;
+    c->host_only = c->opt.device < 0;
+    if (!c->host_only) {
+        DeviceGuard g(c->dev);
+        if (!g.ok) { g_last_error = "cannot select the CUDA device"; return KKT_ERR_CUDA; }
+        kkt_status st = upload(c.get());
+        if (st != KKT_OK) {
+            kkt_destroy(c.release());
+            return st;
+        }
+    }
+    *out = c.release();
     return KKT_OK;
 }
 

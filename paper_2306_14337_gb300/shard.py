@@ -31,3 +31,31 @@ def lpt_assign(costs, world: int):
         out[r].append(i)
         heapq.heappush(heap, (load + float(costs[i]), r))
     return [sorted(v) for v in out]
+
+
+class RankLost(RuntimeError):
+    """Ranks that did not reach a step of a multi-rank run in time."""
+
+    def __init__(self, step, ranks):
+        super().__init__(f"ranks {ranks} did not reach step {step}")
+        self.step = step
+        self.ranks = list(ranks)
+
+
+def step_barrier(store, rank: int, world: int, step: int, timeout_s: float = 10.0):
+    """Announce that this rank reached ``step`` and wait, on the host, until
+    every rank has announced it; raise RankLost naming the ranks that did not
+    within ``timeout_s``.  Called between steps (no kernel or collective of
+    this rank in flight), so a rank that failed or left is detected before
+    the survivors launch the next step.  ``store`` is a torch.distributed
+    Store shared by the ranks (e.g. the one of the rendezvous)."""
+    from datetime import timedelta
+    store.set(f"kkt/step/{step}/{rank}", "1")
+    missing = []
+    for r in range(world):
+        try:
+            store.wait([f"kkt/step/{step}/{r}"], timedelta(seconds=timeout_s))
+        except Exception:                      # the store reports a timeout as an exception
+            missing.append(r)
+    if missing:
+        raise RankLost(step, missing)

@@ -139,6 +139,46 @@ class KKTSolver:
               "kkt_export_row_perm")
         return q
 
+    def save_analysis(self) -> bytes:
+        """The analysis as a checksummed image (kkt_save_analysis)."""
+        size = C.c_size_t(0)
+        check(self._lib.kkt_save_analysis(self._h, None, 0, C.byref(size)), "kkt_save_analysis")
+        buf = C.create_string_buffer(size.value)
+        check(self._lib.kkt_save_analysis(self._h, buf, size.value, C.byref(size)), "kkt_save_analysis")
+        return buf.raw[: size.value]
+
+    @classmethod
+    def from_analysis(cls, image: bytes, indptr, indices, **opts):
+        """A context from a saved analysis image (kkt_load_analysis) instead of
+        a new analysis; indptr/indices are the caller's pattern (kept for the
+        binding's checks), opts as for the constructor (ordering options are
+        fixed by the image)."""
+        obj = cls.__new__(cls)
+        obj._lib = _capi.load()
+        obj._rp, obj._ci = _i32(indptr), _i32(indices)
+        obj.n = int(obj._rp.size - 1)
+        obj.nnz = int(obj._ci.size)
+        opt = _capi.Options()
+        obj._lib.kkt_default_options(C.byref(opt))
+        for k, v in opts.items():
+            if k == "device":
+                continue
+            if k == "refine_mode":
+                v = _REFINE[v]
+            setattr(opt, k, int(v) if isinstance(v, bool) else v)
+        dev = opts.get("device", 0)
+        obj.device = None if dev is None else torch.device("cuda", int(dev))
+        opt.device = -1 if dev is None else int(dev)
+        obj.fp32 = bool(opts.get("factor_fp32", False))
+        obj._perm = obj._row_perm = None
+        obj._opt = opt
+        h = C.c_void_p()
+        check(obj._lib.kkt_load_analysis(image, len(image), C.byref(opt), C.byref(h)), "kkt_load_analysis")
+        obj._h = h
+        obj._values = None
+        obj.version = 0
+        return obj
+
     def reanalyze(self, values):
         """Analyze again with the given host values (kkt_analyze_values: a new
         max-product matching and ordering), replacing this context; the other

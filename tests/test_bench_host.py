@@ -54,3 +54,12 @@ def test_timing_rules_are_enforced():
 def test_native_arm_needs_a_gpu():
     out = _run("--steps", "1", "--warmup", "3", "--no-cpu-baseline", "--no-variants")
     assert out.returncode != 0 and "GPU" in (out.stdout + out.stderr)
+
+
+def test_reference_arm_of_the_batched_workload():
+    out = _run("--impl", "reference", "--steps", "1", "--warmup", "3", "--workload", "10000bus_x64_batched",
+               "--ref-budget", "2", "--cpu-budget", "2")
+    assert out.returncode == 0, out.stderr
+    d = json.loads([l for l in out.stdout.splitlines() if l.strip().startswith("{")][-1])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "10000bus_x64_batched"
+    assert "scenario systems" in d["cpu_baseline"]["sample"]

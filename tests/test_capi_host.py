@@ -180,3 +180,27 @@ def test_stats_byte_and_flop_counts():
     lcount = np.bincount(ci[lower], minlength=n)
     assert st["flops_refactor"] == float(np.sum(lcount * (1 + 2 * lcount)))
     assert st["bytes_refactor"] == 12.0 * s.nnz + 12.0 * st["nnz_lu"] + 4.0 * (n + 1) + 4.0 * st["nnz_lu"]
+
+
+def test_analysis_checkpoint_round_trip_and_corruption():
+    """kkt_save_analysis / kkt_load_analysis on host-only contexts: the loaded
+    context exports the same ordering, pattern, levels and statistics; a
+    flipped byte or a truncated image is refused."""
+    from kktgen import config_sequence
+    from paper_2306_14337_gb300 import KKTSolver, _capi
+    s = config_sequence(0)
+    A = KKTSolver(s.n, s.indptr, s.indices, device=None)
+    img = A.save_analysis()
+    B = KKTSolver.from_analysis(img, s.indptr, s.indices, device=None)
+    ea, eb = A.export_symbolic(), B.export_symbolic()
+    for k in ea:
+        assert np.array_equal(ea[k], eb[k]), k
+    sa, sb = A.stats(), B.stats()
+    for k in ("n", "nnz_lu", "n_levels", "n_levels_u", "max_row", "flops_refactor", "n_tasks", "max_task"):
+        assert sa[k] == sb[k], k
+    bad = bytearray(img)
+    bad[len(bad) // 2] ^= 0x40
+    for broken in (bytes(bad), img[:-9]):
+        with pytest.raises(_capi.KKTError) as e:
+            KKTSolver.from_analysis(broken, s.indptr, s.indices, device=None)
+        assert e.value.status == _capi.KKT_ERR_ARG

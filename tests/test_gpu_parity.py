@@ -418,3 +418,20 @@ def test_random_patterns(n, density, seed):
     x = S.solve(_t(b))
     S.refine(_t(b), x)
     assert oracle.omega(n, rp, ci, v, b, x.cpu().numpy()) <= 1e-14
+
+
+def test_loaded_analysis_factors_bit_identically():
+    """A context resumed from a saved analysis image (kkt_load_analysis) gives
+    the same factors, bit for bit, as the context that saved it (the row
+    updates are applied in a fixed order, so the refactorization is
+    deterministic)."""
+    s = _seq(1)
+    A = KKTSolver(s.n, s.indptr, s.indices)
+    B = KKTSolver.from_analysis(A.save_analysis(), s.indptr, s.indices)
+    v = _t(s.values(5))
+    A.refactor(v)
+    B.refactor(v)
+    assert torch.equal(A.export_factors(), B.export_factors())
+    b = _t(s.rhs(5))
+    x = B.solve(b)
+    assert B.refine(b, x)["converged"]

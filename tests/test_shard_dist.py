@@ -91,3 +91,37 @@ def test_two_rank_sharded_solve_matches_single_process():
         x, *_ = o.refine(rhs)
         assert w <= 1e-14
         np.testing.assert_array_equal(np.array(head), x[:5])
+
+
+def _leaving_worker(rank, world, port, q):
+    import datetime
+    import torch.distributed as dist
+    from paper_2306_14337_gb300.shard import RankLost, step_barrier
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timeout=datetime.timedelta(seconds=30))
+    try:
+        for step in range(3):
+            if rank == 1 and step == 1:
+                q.put(("left", rank, step))    # leaves between steps: nothing of it is in flight
+                return
+            step_barrier(store, rank, world, step, timeout_s=3.0)
+            q.put(("done", rank, step))
+    except RankLost as e:
+        q.put(("lost", rank, e.step, e.ranks))
+
+
+def test_rank_that_leaves_between_steps_is_reported():
+    """A rank that exits between steps: the survivor's next step barrier (on
+    the host, before any launch of that step) names it instead of hanging."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_leaving_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    events = [q.get(timeout=120) for _ in range(4)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert ("done", 0, 0) in events and ("done", 1, 0) in events
+    assert ("left", 1, 1) in events
+    assert ("lost", 0, 1, [1]) in events
