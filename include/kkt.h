@@ -120,6 +120,23 @@ typedef struct {
     const int *user_row_perm; /* NULL, or a host array of n rows: the context then
                                factors Q A, whose row j is row user_row_perm[j] of A
                                (copied during analysis; see kkt_analyze_values) */
+    int dense_block;        /* dense root block (Sec. 4, supernodal methods: dense
+                               blocks where the factor is dense): the last k rows of
+                               the elimination order are stored as a full k x k block
+                               of the factor (explicit zeros where the fill pattern has
+                               none) and, after the sparse rows, factored by a blocked
+                               dense LU with the same fixed pivots and perturbation
+                               test.  -1: none; 0 (default): the largest trailing
+                               block of at most 2,048 rows whose pattern is at least
+                               80% full, if it has 96 rows or more; k > 0: k rows.
+                               The block is the top of one path of the elimination
+                               tree (each row the parent of the one before), so k is
+                               capped at that path's length (the forward levels of
+                               the tree).  The exported pattern (kkt_export_symbolic)
+                               then holds the whole block; its entries outside the
+                               fill pattern of the oracle's definition are exactly
+                               zero.  Used by kkt_refactor; the batched and queued
+                               refactorizations treat the block's rows as sparse rows. */
 } kkt_options;
 
 typedef struct {
@@ -148,6 +165,7 @@ typedef struct {
     int refactor_big_warps; /* warps per CTA of the refactorization that take the
                                rows longer than 1,024 entries (0: no such rows) */
     int refactor_big_cap;   /* row capacity (entries) of those warps' shared memory */
+    int dense_rows;         /* rows of the dense root block (0: none) */
 } kkt_stats;
 
 typedef struct {
@@ -302,6 +320,16 @@ kkt_status kkt_get_stats(const kkt_ctx *ctx, kkt_stats *stats);
  */
 kkt_status kkt_export_symbolic(const kkt_ctx *ctx, int *perm, int *lu_row_ptr,
                                int *lu_col_idx, int *level, int *level_u);
+
+/*
+ * Rows of the dense root block (options.dense_block; Sec. 4 on supernodal
+ * dense blocks), numbered like kkt_export_symbolic, in their elimination
+ * order: rows[0 .. dense_rows-1] (dense_rows from kkt_get_stats; nothing is
+ * written when it is 0).  The exported pattern is the fill pattern of the
+ * ordering plus every (rows[a], rows[b]).  Host only.  KKT_ERR_ARG for a
+ * NULL context, or NULL rows when the block is not empty.
+ */
+kkt_status kkt_export_dense_rows(const kkt_ctx *ctx, int *rows);
 
 /*
  * Checkpoint and resume of the analysis (Sec. 4 and Sec. 5.2: one symbolic

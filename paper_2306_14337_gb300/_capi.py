@@ -52,6 +52,7 @@ class Options(C.Structure):
         ("symmetric", C.c_int),
         ("jacobi_sweeps", C.c_int),
         ("user_row_perm", C.POINTER(C.c_int)),
+        ("dense_block", C.c_int),
     ]
 
 
@@ -81,6 +82,7 @@ class Stats(C.Structure):
         ("max_task", C.c_int),
         ("refactor_big_warps", C.c_int),
         ("refactor_big_cap", C.c_int),
+        ("dense_rows", C.c_int),
     ]
 
 
@@ -137,6 +139,7 @@ SIGNATURES = {
     "kkt_analyze_values": (C.c_int, [C.c_int, _ip, _ip, C.POINTER(C.c_double), C.POINTER(Options),
                                      C.POINTER(_vp)]),
     "kkt_export_row_perm": (C.c_int, [_vp, _ip]),
+    "kkt_export_dense_rows": (C.c_int, [_vp, _ip]),
     "kkt_save_analysis": (C.c_int, [_vp, _vp, C.c_size_t, C.POINTER(C.c_size_t)]),
     "kkt_load_analysis": (C.c_int, [_vp, C.c_size_t, C.POINTER(Options), C.POINTER(_vp)]),
 }

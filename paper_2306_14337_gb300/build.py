@@ -28,7 +28,7 @@ def _nvcc():
 
 
 def sources():
-    return [os.path.join(CSRC, f) for f in ("analysis.cpp", "kkt.cu", "noalloc.cu", "probe.cu")] + [
+    return [os.path.join(CSRC, f) for f in ("analysis.cpp", "kkt.cu", "dense.cu", "noalloc.cu", "probe.cu")] + [
         os.path.join(CSRC, f) for f in ("analysis.h", "kernels.cuh")] + [os.path.join(INCLUDE, "kkt.h")]
 
 
@@ -49,6 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     o_dev = os.path.join(OUT_DIR, f"kkt.{tag}.o")
     o_na = os.path.join(OUT_DIR, f"noalloc.{tag}.o")
     o_pr = os.path.join(OUT_DIR, f"probe.{tag}.o")
+    o_dn = os.path.join(OUT_DIR, f"dense.{tag}.o")
     cuda = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-c"]
     cmds = [
         ["g++", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE, "-c", os.path.join(CSRC, "analysis.cpp"),
@@ -56,6 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cuda + [os.path.join(CSRC, "kkt.cu"), "-o", o_dev],
         cuda + [os.path.join(CSRC, "noalloc.cu"), "-o", o_na],
         cuda + [os.path.join(CSRC, "probe.cu"), "-o", o_pr],
+        cuda + [os.path.join(CSRC, "dense.cu"), "-o", o_dn],
     ]
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for c in cmds]
     outs = [p.communicate()[0] for p in procs]
@@ -65,14 +67,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.returncode:
             raise RuntimeError(f"compile failed: {c[0]} ({p.returncode})")
     tmp = LIB + f".{tag}.tmp"
-    link = [nvcc, "-shared", *ARCH, "-o", tmp, o_host, o_dev, o_na, o_pr, "-lpthread", "-ldl"]
+    link = [nvcc, "-shared", *ARCH, "-o", tmp, o_host, o_dev, o_na, o_pr, o_dn, "-lpthread", "-ldl"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if verbose or r.returncode:
         sys.stderr.write(" ".join(link) + "\n" + r.stdout)
     if r.returncode:
         raise RuntimeError("link failed")
     os.replace(tmp, LIB)
-    for o in (o_host, o_dev, o_na, o_pr):
+    for o in (o_host, o_dev, o_na, o_pr, o_dn):
         os.remove(o)
     return LIB
 

@@ -266,7 +266,7 @@ static void etree_heights(int n, const std::vector<int> &grp, const std::vector<
 }
 
 int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
-            Analysis &out, std::string &err, long long map_budget_bytes) {
+            Analysis &out, std::string &err, long long map_budget_bytes, int dense_req) {
     int rc = validate_pattern(n, rp, ci);
     if (rc) { err = "malformed CSR pattern (n <= 0, unsorted, duplicate or out-of-range index)"; return rc; }
     if (rp[n] > (1 << 30)) { err = "too many entries"; return A_ERR_ARG; }
@@ -395,6 +395,56 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
         std::sort(lci.begin() + start, lci.end());
         lrp[i + 1] = (int)lci.size();
     }
+    // Dense root block (Sec. 4: supernodal factorizations; the top of the
+    // elimination tree of these KKT matrices is a chain of separator rows
+    // whose trailing block is nearly full).  Rows [lo, n) get every column of
+    // [lo, i) in their L part, so the trailing s x s block is full; fill stays
+    // closed (a pivot d >= lo only updates rows and columns >= lo), rows below
+    // lo are unchanged, and the block becomes a chain of the tree.
+    {
+        int s = 0;
+        if (dense_req > 0) {
+            s = std::min(dense_req, n);
+        } else if (dense_req == 0) {
+            // entries of the trailing block of t rows: t + 2 |{L(i,j): i, j >= n - t}|;
+            // adding row n - t - 1 adds the entries of its L column
+            std::vector<int> lcol(n, 0);
+            for (size_t q = 0; q < lci.size(); q++) lcol[lci[q]]++;
+            long long cnt = 0;
+            const int tmax = std::min(n, DENSE_MAX_ROWS);
+            for (int t = 1; t <= tmax; t++) {
+                cnt += lcol[n - t];
+                if ((double)(t + 2 * cnt) >= DENSE_MIN_DENSITY * (double)t * (double)t) s = t;
+            }
+            if (s < DENSE_MIN_ROWS) s = 0;
+        }
+        // The block must be a chain of the elimination tree (each row the
+        // child of the next): then every order of the tree's postorders and
+        // of the caller's ordering agrees on it, and the full block changes
+        // the factorization of that order by explicit zeros only.  The
+        // relabelling put the longest path from the last root at the end.
+        int chain = 1;
+        while (chain < n && a.parent[n - chain - 1] == n - chain) chain++;
+        s = std::min(s, chain);
+        if (dense_req == 0 && s < DENSE_MIN_ROWS) s = 0;
+        a.dense_rows = s;
+        if (s > 0) {
+            const int lo = n - s;
+            std::vector<int> nrp(n + 1, 0), nci;
+            nci.reserve(lci.size() + (size_t)s * (size_t)s / 2);
+            for (int i = 0; i < n; i++) {
+                for (int p = lrp[i]; p < lrp[i + 1]; p++)
+                    if (i < lo || lci[p] < lo) nci.push_back(lci[p]);
+                if (i >= lo)
+                    for (int j = lo; j < i; j++) nci.push_back(j);
+                nrp[i + 1] = (int)nci.size();
+            }
+            lrp.swap(nrp);
+            lci.swap(nci);
+            for (int i = lo; i < n - 1; i++) a.parent[i] = i + 1;
+            a.parent[n - 1] = -1;
+        }
+    }
     // rows of U = columns of L (pattern symmetric)
     std::vector<int> ucnt(n + 1, 0);
     for (size_t q = 0; q < lci.size(); q++) ucnt[lci[q] + 1]++;
@@ -506,26 +556,26 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
 
     // update maps: one uint16 per multiply-add of the refactorization; rows
     // are independent, so they are filled in parallel after a prefix sum
+    // (the dense root block's own pivot steps -- row and pivot both in the
+    // block -- run in the dense kernel and have no map entries)
     a.upd_off.clear();
     a.upd_map.clear();
     {
-        double entries = 0.0;
-        for (int d = 0; d < n; d++) {
-            const double lcol = ucnt[d + 1] - ucnt[d];
-            entries += lcol * lcol;
+        const int dlo = n - a.dense_rows;
+        std::vector<long long> rowq(n + 1, 0);
+        for (int i = 0; i < n; i++) {
+            long long c = 0;
+            for (int t = a.lu_rp[i]; t < a.diag[i]; t++) {
+                const int d = a.lu_ci[t];
+                if (i >= dlo && d >= dlo) break;
+                c += a.lu_rp[d + 1] - a.diag[d] - 1;
+            }
+            rowq[i + 1] = rowq[i] + c;
         }
+        const double entries = (double)rowq[n];
         const bool fits = a.max_row <= 65535 && entries < 4.0e9 &&
                           entries * 2.0 + 4.0 * (double)nnz <= (double)map_budget_bytes;
         if (fits) {
-            std::vector<long long> rowq(n + 1, 0);
-            for (int i = 0; i < n; i++) {
-                long long c = 0;
-                for (int t = a.lu_rp[i]; t < a.diag[i]; t++) {
-                    const int d = a.lu_ci[t];
-                    c += a.lu_rp[d + 1] - a.diag[d] - 1;
-                }
-                rowq[i + 1] = rowq[i] + c;
-            }
             a.upd_off.assign(nnz, 0);
             a.upd_map.resize((size_t)rowq[n]);
             std::atomic<int> bad{0};
@@ -536,6 +586,7 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
                     for (int t = rb; t < a.diag[i]; t++) {
                         const int d = a.lu_ci[t];
                         a.upd_off[t] = (unsigned)q;
+                        if (i >= dlo && d >= dlo) continue;
                         int w = t + 1;               // merge U(d, >d) into row i (both sorted)
                         for (int u = a.diag[d] + 1; u < a.lu_rp[d + 1]; u++) {
                             const int j = a.lu_ci[u];

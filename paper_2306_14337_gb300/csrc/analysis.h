@@ -51,7 +51,22 @@ struct Analysis {
     // U(d, >d) start inside upd_map (empty when over budget).
     std::vector<unsigned> upd_off;
     std::vector<unsigned short> upd_map;
+    // Dense root block: the last dense_rows rows (internal labelling) are
+    // stored as a full square block of the combined pattern (its structural
+    // zeros become explicit slots), so that their elimination among
+    // themselves runs as a blocked dense LU.  0 = no such block.  The block
+    // is the top of a path of the elimination tree (at most as many rows as
+    // the path from the last root down its deepest children).  Rows below
+    // the block never depend on it; the update maps hold no entries for the
+    // block's own pivot steps (rows and pivots both inside the block).
+    int dense_rows = 0;
 };
+
+// Largest trailing block the automatic choice considers, the density it
+// requires and the smallest block it keeps.
+constexpr int DENSE_MAX_ROWS = 2048;
+constexpr double DENSE_MIN_DENSITY = 0.8;
+constexpr int DENSE_MIN_ROWS = 96;
 
 // Status codes match kkt_status.
 enum { A_OK = 0, A_ERR_ARG = 1, A_ERR_PATTERN = 2, A_ERR_ALLOC = 3 };
@@ -77,7 +92,12 @@ int max_product_matching(int n, const int *rp, const int *ci, const double *val,
                          std::vector<int> &row_of_col, std::string &err);
 
 // Full analysis.  ordering: 0 AMD, 1 natural, 2 user (user_perm, new -> old).
+// dense_req: -1 no dense root block; 0 the automatic choice (the largest
+// trailing block of at most DENSE_MAX_ROWS rows whose pattern is at least
+// DENSE_MIN_DENSITY full, if it has DENSE_MIN_ROWS rows or more); k > 0
+// k rows.  Either is capped at the length of the path of the elimination
+// tree that ends the internal order.
 int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
-            Analysis &out, std::string &err, long long map_budget_bytes = 0);
+            Analysis &out, std::string &err, long long map_budget_bytes = 0, int dense_req = -1);
 
 }  // namespace kkt

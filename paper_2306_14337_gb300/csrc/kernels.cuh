@@ -61,6 +61,10 @@ struct DevPattern {
     int n_free, n_long;
     const unsigned *upd_off;             // update maps (null when not built)
     const unsigned short *upd_map;
+    // First row of the dense root block (n: none).  The update maps hold no
+    // entries for the block's own pivot steps (row and pivot both >= dense_lo);
+    // kernels that take those steps as sparse steps search the row instead.
+    int dense_lo;
 };
 
 struct TaskCfg {
@@ -116,7 +120,25 @@ struct RunCfg {
     long long trace_stride;      // words per phase region
     int unpublished_row;         // failure-detection test: this row is never published (-1: none)
     unsigned poll_ns_max;        // backoff cap of a waiting lane (ns)
+    // Dense root block (single-system refactorization only): rows >= dense_lo
+    // take only their pivot steps below the block and leave their partly
+    // reduced block row in dense (row-major, leading dimension dense_ld);
+    // k_dense_lu then factors the block.  dense_lo = INT_MAX: no block.
+    int dense_lo;
+    int dense_ld;
+    void *dense;
+    unsigned *dense_bar;         // grid barrier of k_dense_lu: {arrivals, generation}
 };
+
+// Launch k_dense_lu<T> (csrc/dense.cu) on `grid` co-resident CTAs: the
+// blocked LU of the dense root block left in rc.dense by the refactorization,
+// with the FP64 pivot test, then the block's factors written to LU (and its
+// transposed copy LUT) and its reciprocal pivots to rcp.
+template <typename T>
+cudaError_t launch_dense_lu(const DevPattern &P, const RunCfg &rc, const double *aval, const double *sp,
+                            T *LU, T *LUT, T *rcp, double tau_rel, int grid, cudaStream_t stream);
+int dense_lu_threads();
+cudaError_t dense_lu_per_sm(int fp32, int *per_sm);
 
 // Record the text returned by kkt_last_error() on the calling thread (every
 // translation unit of the library reports through this one store).

@@ -288,6 +288,21 @@ template <typename T> struct Strided {
     __device__ __forceinline__ T &operator[](long long k) const { return p[k * B + s]; }
 };
 
+// A row of the dense root block after its pivot steps below the block: its
+// multipliers go to their slots (and the transposed copy); its block part,
+// the row's last P.n - dense_lo entries, goes to the dense array for
+// k_dense_lu.  Nothing is published: only rows of the block read the block.
+template <typename T, typename TP>
+__device__ __forceinline__ void dense_row_out(const DevPattern &P, const RunCfg &rc, TP LU, TP LUT,
+                                              const T *w, int rb, int len, int nst, int i, int lane) {
+    T *D = reinterpret_cast<T *>(rc.dense) + (size_t)(i - rc.dense_lo) * rc.dense_ld;
+    for (int c = lane; c < len - nst; c += 32) D[c] = w[nst + c];
+    for (int t = lane; t < nst; t += 32) {
+        LU[rb + t] = w[t];
+        LUT[P.tpos[rb + t]] = w[t];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // numeric refactorization: one warp per row of L+U (Algorithm 1's row-wise
 // elimination, fixed pivots), rows claimed deepest first (distance to the root).
@@ -312,6 +327,12 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                                              int cap, int gw, int lane) {
     const bool mapped = P.upd_off != nullptr;
             const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
+            // a row of the dense root block takes only the pivot steps below the block
+            const bool dense = i >= rc.dense_lo;
+            const int nst = dense ? len - (P.n - rc.dense_lo) : dp;
+            // steps t >= tmap (pivots inside the dense root block, when the kernel
+            // takes them as sparse steps) have no update map
+            const int tmap = i >= P.dense_lo ? len - (P.n - P.dense_lo) : INT_MAX;
             const int *c = P.lu_ci + rb;
             T *w;
             if (len <= cap) {
@@ -339,7 +360,7 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
             auto load_meta = [&](int t0) {
                 md = mub = mue = 0;
                 mmo = 0;
-                if (t0 + lane < dp) {
+                if (t0 + lane < nst) {
                     md = P.lu_ci[rb + t0 + lane];
                     mub = P.diag[md];
                     mue = P.lu_rp[md + 1];
@@ -347,7 +368,7 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                 }
             };
             auto target = [&](int t, int ub, unsigned mo, int u) -> int {
-                if (mapped) return P.upd_map[mo + (u - ub - 1)];
+                if (mapped && t < tmap) return P.upd_map[mo + (u - ub - 1)];
                 const int j = P.lu_ci[u];
                 int a_ = t + 1, b_ = len;
                 while (a_ < b_) {
@@ -375,12 +396,12 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                     }
                 }
             };
-            if (dp > 0) {
+            if (nst > 0) {
                 load_meta(0);
                 prefetch(0, __shfl_sync(FULL, md, 0), __shfl_sync(FULL, mub, 0), __shfl_sync(FULL, mue, 0),
                          __shfl_sync(FULL, mmo, 0));
             }
-            for (int t = 0; t < dp; t++) {
+            for (int t = 0; t < nst; t++) {
                 const int k = t & 31;
                 const int d = __shfl_sync(FULL, md, k);
                 const int ub = __shfl_sync(FULL, mub, k);
@@ -392,7 +413,7 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
     #pragma unroll
                 for (int q = 0; q < UJ; q++) { lo[q] = plo[q]; uv[q] = pu[q]; }
                 // next step's loads go out now
-                if (t + 1 < dp) {
+                if (t + 1 < nst) {
                     if (k == 31) load_meta(t + 1);
                     const int k1 = (t + 1) & 31;
                     prefetch(t + 1, __shfl_sync(FULL, md, k1), __shfl_sync(FULL, mub, k1),
@@ -412,7 +433,7 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                         const T w0 = warp_wait_load(rc, rcp + d, lane == 0, lane);
                         if (lane == 0) r = w0;
                     }
-                    if (t + 1 < dp && __any_sync(FULL, lane == 0 && is_marker(pr))) {
+                    if (t + 1 < nst && __any_sync(FULL, lane == 0 && is_marker(pr))) {
                         const int k1 = (t + 1) & 31;
                         const int d1 = __shfl_sync(FULL, md, k1), ub1 = __shfl_sync(FULL, mub, k1),
                                   ue1 = __shfl_sync(FULL, mue, k1);
@@ -507,6 +528,10 @@ __device__ __forceinline__ void refactor_row(const DevPattern &P, const RunCfg &
                 __syncwarp();
                 if (lane == 0) w[t] = l;
             }
+            if (dense) {
+                dense_row_out<T>(P, rc, LU, LUT, w, rb, len, nst, i, lane);
+                return;
+            }
             // pivot test in FP64 (perturb to sign(a_ii) tau and count)
             if (lane == 0) {
                 double pv = (double)w[dp];
@@ -592,6 +617,9 @@ __device__ __forceinline__ void refactor_row_staged(const DevPattern &P, const R
     using S = Stage<T>;
     constexpr int UJ = S::SB / 32;
     const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
+    // a row of the dense root block takes only the pivot steps below the block
+    const bool dense = i >= rc.dense_lo;
+    const int nst = dense ? len - (P.n - rc.dense_lo) : dp;
     T *w = len <= cap ? sval : reinterpret_cast<T *>(rc.scratch) + (size_t)gw * rc.scratch_stride;
     const double si = sp[i];
     for (int t = lane; t < len; t += 32) {
@@ -599,7 +627,7 @@ __device__ __forceinline__ void refactor_row_staged(const DevPattern &P, const R
         w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + t]] * aval[k] : 0.0);
     }
     __syncwarp();
-    if (dp > 0) {
+    if (nst > 0) {
         // producer: next unit to stage is block pb of step pt; the metadata of
         // steps c0 .. c0 + 31 (lane k: step c0 + k) and of the chunk after it
         int pt = 0, pb = 0, c0 = 0;
@@ -608,7 +636,7 @@ __device__ __forceinline__ void refactor_row_staged(const DevPattern &P, const R
         auto load_meta = [&](int t0, int &d_, int &ub_, int &ue_, unsigned &mo_) {
             d_ = ub_ = ue_ = 0;
             mo_ = 0;
-            if (t0 + lane < dp) {
+            if (t0 + lane < nst) {
                 d_ = P.lu_ci[rb + t0 + lane];
                 ub_ = P.diag[d_];
                 ue_ = P.lu_rp[d_ + 1];
@@ -619,7 +647,7 @@ __device__ __forceinline__ void refactor_row_staged(const DevPattern &P, const R
         load_meta(32, nd, nub, nue, nmo);
         auto issue = [&](int unit) {
             unsigned char *slot = ring + (unit % S::STAGES) * S::SLOT;
-            if (pt < dp) {
+            if (pt < nst) {
                 if (pt - c0 >= 32) {                    // next metadata chunk
                     c0 += 32;
                     md = nd; mub = nub; mue = nue; mmo = nmo;
@@ -721,11 +749,15 @@ __device__ __forceinline__ void refactor_row_staged(const DevPattern &P, const R
             if (flags & 2) {                            // last block of step t
                 __syncwarp();
                 if (lane == 0) w[t] = l;
-                if (t + 1 == dp) break;
+                if (t + 1 == nst) break;
             }
         }
         cp_async_wait<0>();                             // nothing of this row left in flight
         __syncwarp();
+    }
+    if (dense) {
+        dense_row_out<T>(P, rc, LU, LUT, w, rb, len, nst, i, lane);
+        return;
     }
     // pivot test in FP64 (perturb to sign(a_ii) tau and count)
     if (lane == 0) {
@@ -780,6 +812,9 @@ __device__ __forceinline__ void refactor_row_sym(const DevPattern &P, const RunC
     constexpr int UJ = S::SB / 32;
     const int rb = P.lu_rp[i], len = P.lu_rp[i + 1] - rb, dp = P.diag[i] - rb;
     const int ulen = len - dp;                         // U part, diagonal first
+    // a row of the dense root block takes only the pivot steps below the block
+    const bool dense = i >= rc.dense_lo;
+    const int nst = dense ? len - (P.n - rc.dense_lo) : dp;
     // the row buffer holds the U part only; each multiplier l(i,d) goes to
     // its L slot at once (the address needs no load) and to the transposed
     // factor at the end
@@ -790,14 +825,14 @@ __device__ __forceinline__ void refactor_row_sym(const DevPattern &P, const RunC
         w[t] = (T)((k >= 0) ? si * sp[P.lu_ci[rb + dp + t]] * aval[k] : 0.0);
     }
     __syncwarp();
-    if (dp > 0) {
+    if (nst > 0) {
         int pt = 0, pb = 0, c0 = 0;
         int md = 0, mub = 0, mue = 0, mts = 0, nd = 0, nub = 0, nue = 0, nts = 0;
         unsigned mmo = 0, nmo = 0;
         auto load_meta = [&](int t0, int &d_, int &ub_, int &ue_, int &ts_, unsigned &mo_) {
             d_ = ub_ = ue_ = ts_ = 0;
             mo_ = 0;
-            if (t0 + lane < dp) {
+            if (t0 + lane < nst) {
                 d_ = P.lu_ci[rb + t0 + lane];
                 ub_ = P.diag[d_];
                 ue_ = P.lu_rp[d_ + 1];
@@ -809,7 +844,7 @@ __device__ __forceinline__ void refactor_row_sym(const DevPattern &P, const RunC
         load_meta(32, nd, nub, nue, nts, nmo);
         auto issue = [&](int unit) {
             unsigned char *slot = ring + (unit % S::STAGES) * S::SLOT;
-            if (pt < dp) {
+            if (pt < nst) {
                 if (pt - c0 >= 32) {
                     c0 += 32;
                     md = nd; mub = nub; mue = nue; mts = nts; mmo = nmo;
@@ -908,10 +943,17 @@ __device__ __forceinline__ void refactor_row_sym(const DevPattern &P, const RunC
 #pragma unroll
             for (int q = 0; q < UJ; q++)
                 if (lo[q] >= 0) w[lo[q]] = x[q] - l * uv[q];
-            if ((flags & 2) && t + 1 == dp) break;
+            if ((flags & 2) && t + 1 == nst) break;
         }
         cp_async_wait<0>();
         __syncwarp();
+    }
+    if (dense) {                       // the block row's upper part; k_dense_lu mirrors it
+        const int r = i - rc.dense_lo;
+        T *D = reinterpret_cast<T *>(rc.dense) + (size_t)r * rc.dense_ld + r;
+        for (int t = lane; t < ulen; t += 32) D[t] = w[t];
+        for (int t = lane; t < nst; t += 32) LUT[P.tpos[rb + t]] = LU[rb + t];
+        return;
     }
     // pivot test in FP64 (perturb to sign(a_ii) tau and count), sign for the inertia
     if (lane == 0) {
@@ -2306,6 +2348,9 @@ struct kkt_ctx {
     double *d_qvals = nullptr;       // values of Q A (nnz)
     double *d_qvec = nullptr;        // 2 n: Q b, and Q lambda
     double *d_qdA = nullptr;         // gradient on the entries of Q A (nnz)
+    void *d_dense = nullptr;         // dense root block (dense_rows x dense_ld words)
+    unsigned *d_dense_bar = nullptr; // grid barrier of k_dense_lu
+    int dense_ld = 0, dense_grid = 0;
     bool factored = false;
     int last_iters = 0;
     double last_omega = -1.0;
@@ -2399,6 +2444,7 @@ void kkt_default_options(kkt_options *o) {
     o->symmetric = 0;
     o->jacobi_sweeps = 8;
     o->user_row_perm = nullptr;
+    o->dense_block = 0;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -2479,6 +2525,7 @@ static kkt_status upload(kkt_ctx *c) {
     c->P.nnz_a = nnza;
     c->P.n_free = (int)ord_free.size();
     c->P.n_long = (int)ord_long.size();
+    c->P.dense_lo = n - a.dense_rows;
 
     const bool f32 = c->opt.factor_fp32 != 0;
     const size_t tsz = f32 ? sizeof(float) : sizeof(double);
@@ -2936,6 +2983,26 @@ static kkt_status upload(kkt_ctx *c) {
     c->rc.sched = c->d_sched;
     c->rc.cap = cap;
     c->rc.scratch = c->d_scratch;
+    // dense root block: its dense array (row-major, leading dimension a multiple
+    // of 32 words) and the barrier word of k_dense_lu; the shared RunCfg keeps
+    // the block off (the batched and queued kernels factor its rows as rows)
+    c->rc.dense_lo = INT_MAX;
+    c->rc.dense_ld = 0;
+    c->rc.dense = nullptr;
+    c->rc.dense_bar = nullptr;
+    if (a.dense_rows > 0) {
+        const int sd = a.dense_rows;
+        c->dense_ld = (sd + 31) / 32 * 32;
+        const size_t db = (size_t)sd * c->dense_ld * tsz;
+        CK(cudaMalloc(&c->d_dense, db));
+        CK(cudaMalloc(&c->d_dense_bar, 256));
+        CK(cudaMemset(c->d_dense_bar, 0, 256));
+        c->device_bytes += db + 256;
+        int per = 0;
+        CK(dense_lu_per_sm(f32 ? 1 : 0, &per));
+        if (per < 1) { g_last_error = "dense block kernel does not fit on an SM"; return KKT_ERR_CUDA; }
+        c->dense_grid = sms;             // one CTA per SM, all resident (cooperative launch)
+    }
     if (c->rowperm) {
         const size_t nnz = c->qmap.size();
         CK(cudaMalloc(&c->d_q, (size_t)n * sizeof(int)));
@@ -2986,6 +3053,8 @@ void kkt_destroy(kkt_ctx *c) {
         cudaFree(c->b_norms);
         cudaFreeHost(c->hb_norms);
         cudaFree(c->d_scratch);
+        cudaFree(c->d_dense);
+        cudaFree(c->d_dense_bar);
         cudaFreeHost(c->h_norms);
     }
     delete c;
@@ -3003,7 +3072,7 @@ static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, con
     if (opt) c->opt = *opt; else kkt_default_options(&c->opt);
     if (c->opt.fgmres_restart < 1 || c->opt.max_refine < 0 || c->opt.spin_limit < 1 ||
         c->opt.refine_mode < KKT_REFINE_CLASSIC || c->opt.refine_mode > KKT_REFINE_FGMRES_JACOBI ||
-        c->opt.jacobi_sweeps < 0 ||
+        c->opt.jacobi_sweeps < 0 || c->opt.dense_block < -1 ||
         c->opt.max_batch < 1 || c->opt.cta_warps < 0 || c->opt.refactor_ctas < 0 ||
         c->opt.solve_ctas < 0) {
         g_last_error = "invalid option";
@@ -3064,7 +3133,7 @@ static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, con
             rp = qa_rp.data();
             ci = qa_ci.data();
         }
-        rc = analyze(n, rp, ci, c->opt.ordering, c->opt.user_perm, c->an, err, budget);
+        rc = analyze(n, rp, ci, c->opt.ordering, c->opt.user_perm, c->an, err, budget, c->opt.dense_block);
     } catch (const std::bad_alloc &) {
         g_last_error = "host allocation failed during analysis";
         return KKT_ERR_ALLOC;
@@ -3134,11 +3203,23 @@ template <typename T> static kkt_status launch_refactor(kkt_ctx *c, cudaStream_t
     // every entry starts as the not-ready marker; published entries overwrite it
     CK(cudaMemsetAsync(c->d_lu, 0xff, (size_t)c->nnz_lu * sizeof(T), s));
     CK(cudaMemsetAsync(c->d_rcp, 0xff, (size_t)c->an.n * sizeof(T), s));
-    k_refactor<T><<<c->rgrid, c->cta_warps * 32, c->rsmem, s>>>(c->P, c->rc, c->values, c->d_sp,
+    RunCfg rc = c->rc;
+    if (c->an.dense_rows > 0) {          // rows of the dense root block stop below it
+        rc.dense_lo = c->an.n - c->an.dense_rows;
+        rc.dense_ld = c->dense_ld;
+        rc.dense = c->d_dense;
+        rc.dense_bar = c->d_dense_bar;
+    }
+    k_refactor<T><<<c->rgrid, c->cta_warps * 32, c->rsmem, s>>>(c->P, rc, c->values, c->d_sp,
                                                                (T *)c->d_lu, (T *)c->d_lut,
                                                                (T *)c->d_rcp, c->tau_rel);
     CK(cudaGetLastError());
     c->launches++;
+    if (c->an.dense_rows > 0) {
+        CK(launch_dense_lu<T>(c->P, rc, c->values, c->d_sp, (T *)c->d_lu, (T *)c->d_lut, (T *)c->d_rcp,
+                              c->tau_rel, c->dense_grid, s));
+        c->launches++;
+    }
     return pack_tiles<T>(c, s);
 }
 
@@ -4313,6 +4394,7 @@ kkt_status kkt_get_stats(const kkt_ctx *c, kkt_stats *o) {
     o->update_map_entries = (long long)a.upd_map.size();
     o->n_tasks = (int)a.task_lo.size();
     o->max_task = a.max_task;
+    o->dense_rows = a.dense_rows;
     return KKT_OK;
 }
 
@@ -4324,7 +4406,7 @@ kkt_status kkt_get_stats(const kkt_ctx *c, kkt_stats *o) {
 // of all preceding bytes.
 namespace {
 constexpr unsigned kImgMagic = 0x41544b4bu;   // "KKTA"
-constexpr unsigned kImgVersion = 1;
+constexpr unsigned kImgVersion = 2;
 
 struct ImgWriter {
     std::vector<unsigned char> out;
@@ -4380,6 +4462,7 @@ kkt_status kkt_save_analysis(const kkt_ctx *c, void *buf, size_t cap, size_t *si
     w.vec(a.task_lo); w.vec(a.task_hi); w.vec(a.upd_off); w.vec(a.upd_map);
     w.val(a.n_levels); w.val(a.n_levels_u); w.val(a.nnz_sym); w.val(a.max_row); w.val(a.flops);
     w.val(a.max_task);
+    w.val(a.dense_rows);
     w.val<int>(c->rowperm ? 1 : 0);
     w.vec(c->q); w.vec(c->qmap);
     w.val(fnv1a(w.out.data(), w.out.size()));
@@ -4418,6 +4501,7 @@ kkt_status kkt_load_analysis(const void *buf, size_t size, const kkt_options *op
         r.vec(a.task_lo); r.vec(a.task_hi); r.vec(a.upd_off); r.vec(a.upd_map);
         a.n_levels = r.val<int>(); a.n_levels_u = r.val<int>(); a.nnz_sym = r.val<long long>();
         a.max_row = r.val<int>(); a.flops = r.val<double>(); a.max_task = r.val<int>();
+        a.dense_rows = r.val<int>();
         c->rowperm = r.val<int>() != 0;
         r.vec(c->q); r.vec(c->qmap);
         // the sizes the kernels rely on
@@ -4434,6 +4518,13 @@ kkt_status kkt_load_analysis(const void *buf, size_t size, const kkt_options *op
         for (long long k = 0; ok && k < nlu; k++)
             ok = a.lu_ci[k] >= 0 && a.lu_ci[k] < n && a.src[k] >= -1 && a.src[k] < nna && a.tpos[k] >= 0 &&
                  a.tpos[k] < nlu && (a.upd_off.empty() || a.upd_off[k] <= a.upd_map.size());
+        // the dense root block: every one of its rows ends in all of its columns
+        ok = ok && a.dense_rows >= 0 && a.dense_rows <= n;
+        for (long long i = n - a.dense_rows; ok && i < n; i++) {
+            const long long t0 = (long long)a.lu_rp[i + 1] - a.dense_rows;
+            ok = t0 >= a.lu_rp[i];
+            for (long long q = 0; ok && q < a.dense_rows; q++) ok = a.lu_ci[t0 + q] == n - a.dense_rows + q;
+        }
         if (!ok) { g_last_error = "analysis image: inconsistent arrays"; return KKT_ERR_ARG; }
     } catch (const std::bad_alloc &) {
         g_last_error = "host allocation failed while loading an analysis";
@@ -4469,6 +4560,13 @@ kkt_status kkt_export_symbolic(const kkt_ctx *c, int *perm, int *lu_row_ptr, int
         if (level) level[v] = a.level[a.internal_of[v]];
         if (level_u) level_u[v] = a.level_u[a.internal_of[v]];
     }
+    return KKT_OK;
+}
+
+kkt_status kkt_export_dense_rows(const kkt_ctx *c, int *rows) {
+    if (!c || (!rows && c->an.dense_rows > 0)) return KKT_ERR_ARG;
+    const Analysis &a = c->an;
+    for (int r = 0; r < a.dense_rows; r++) rows[r] = a.view_of[a.n - a.dense_rows + r];
     return KKT_OK;
 }
 

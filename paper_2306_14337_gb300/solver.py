@@ -50,7 +50,7 @@ class KKTSolver:
                  pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
                  solve_ctas=0, update_map_budget=0, trace=False, max_batch=1, unpublished_row=-1,
                  poll_ns_max=0, refactor_big_warps=0, symmetric=False, jacobi_sweeps=8, values=None,
-                 row_perm=None, device=0):
+                 row_perm=None, dense_block=0, device=0):
         self._lib = _capi.load()
         self.n = int(n)
         self._rp = _i32(indptr)
@@ -81,6 +81,7 @@ class KKTSolver:
         opt.refactor_big_warps = int(refactor_big_warps)
         opt.symmetric = int(bool(symmetric))
         opt.jacobi_sweeps = int(jacobi_sweeps)
+        opt.dense_block = int(dense_block)
         self._row_perm = None
         if row_perm is not None:
             self._row_perm = _i32(row_perm)
@@ -131,6 +132,15 @@ class KKTSolver:
         check(self._lib.kkt_export_symbolic(self._h, P(perm), P(rp), P(ci), P(lev), P(levu)),
               "kkt_export_symbolic")
         return dict(perm=perm, lu_rp=rp, lu_ci=ci, level=lev, level_u=levu)
+
+    def export_dense_rows(self) -> np.ndarray:
+        """Rows of the dense root block in elimination order, numbered like
+        export_symbolic (empty without a block)."""
+        m = self.stats()["dense_rows"]
+        rows = np.zeros(max(m, 1), np.int32)
+        check(self._lib.kkt_export_dense_rows(self._h, rows.ctypes.data_as(C.POINTER(C.c_int))),
+              "kkt_export_dense_rows")
+        return rows[:m]
 
     def export_row_perm(self) -> np.ndarray:
         """Row permutation of the factored matrix (identity without one)."""

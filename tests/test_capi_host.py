@@ -64,7 +64,7 @@ def test_bad_user_permutation_rejected():
 
 
 def _parity(n, rp, ci, perm):
-    S = KKTSolver(n, rp, ci, perm=perm, device=None)
+    S = KKTSolver(n, rp, ci, perm=perm, dense_block=-1, device=None)
     sym = S.export_symbolic()
     vals = np.random.default_rng(0).standard_normal(len(ci))
     o = oracle.Oracle(n, rp, ci, vals, perm, equil=False)
@@ -204,3 +204,78 @@ def test_analysis_checkpoint_round_trip_and_corruption():
         with pytest.raises(_capi.KKTError) as e:
             KKTSolver.from_analysis(broken, s.indptr, s.indices, device=None)
         assert e.value.status == _capi.KKT_ERR_ARG
+
+
+def _brute_levels(n, rp, ci):
+    """Longest dependency chains of a filled pattern, by definition: the
+    forward level of row i is 0 without L entries, else 1 + the largest level
+    of its L columns; the backward level of row i is 0 without U entries right
+    of the diagonal, else 1 + the largest backward level of those columns."""
+    lev = np.zeros(n, np.int64)
+    levu = np.zeros(n, np.int64)
+    for i in range(n):
+        row = ci[rp[i]:rp[i + 1]]
+        low = row[row < i]
+        if low.size:
+            lev[i] = 1 + lev[low].max()
+    for i in range(n - 1, -1, -1):
+        row = ci[rp[i]:rp[i + 1]]
+        up = row[row > i]
+        if up.size:
+            levu[i] = 1 + levu[up].max()
+    return lev, levu
+
+
+@pytest.mark.parametrize("case,req", [("cfg1", 0), ("cfg0", 1), ("cfg0", 33), ("cfg0", 100),
+                                      ("rand200", 200), ("rand200", 500)])
+def test_dense_root_block_pattern(case, req):
+    """A dense root block of req rows at most (0: the automatic choice): the
+    exported pattern is the oracle's fill plus every pair of the block's
+    rows, every block row depends on the one before it (forward levels
+    strictly increase along the block), and the level schedules are those of
+    the enlarged pattern."""
+    from fill_split import fill_slots
+    if case.startswith("cfg"):
+        s = config_sequence(int(case[3:]))
+        n, rp, ci = s.n, s.indptr, s.indices
+    else:
+        n = 200
+        rp, ci = random_sparse_pattern(n, 0.01, 4, drop_diag=0.1)
+    perm = oracle.min_degree(n, rp, ci)
+    S = KKTSolver(n, rp, ci, perm=perm, dense_block=req, device=None)
+    st = S.stats()
+    vals = np.random.default_rng(0).standard_normal(len(ci))
+    o = oracle.Oracle(n, rp, ci, vals, perm, equil=False)
+    orp, oci = o.F.lu_pattern_csr()
+    V = S.export_dense_rows()
+    if req == 0:
+        assert 96 <= st["dense_rows"] <= 2048
+        # the automatic block is at least 80 % full in the oracle's fill
+        inV = np.zeros(n, bool)
+        inV[V] = True
+        rows = np.repeat(np.arange(n), np.diff(orp))
+        assert np.sum(inV[rows] & inV[oci]) >= 0.8 * V.size ** 2
+    elif case.startswith("cfg"):   # one tree: capped at its height
+        assert st["dense_rows"] == min(req, int(o.F.levels()[0].max()) + 1)
+    else:                          # maybe a forest: capped at the path ending the order
+        assert 1 <= st["dense_rows"] <= min(req, int(o.F.levels()[0].max()) + 1)
+    assert V.size == st["dense_rows"] and np.unique(V).size == V.size
+    fill_slots(S, orp, oci)
+    sym = S.export_symbolic()
+    lev, levu = _brute_levels(n, sym["lu_rp"], sym["lu_ci"])
+    assert np.array_equal(sym["level"], lev) and np.array_equal(sym["level_u"], levu)
+    assert np.all(np.diff(sym["level"][V]) >= 1)
+    assert st["nnz_lu"] == len(sym["lu_ci"])
+    # the checkpoint keeps the block
+    B = KKTSolver.from_analysis(S.save_analysis(), rp, ci, device=None)
+    assert B.stats()["dense_rows"] == st["dense_rows"]
+    assert np.array_equal(B.export_dense_rows(), V)
+
+
+def test_dense_root_block_off_and_bad_option():
+    s = config_sequence(1)
+    S = KKTSolver(s.n, s.indptr, s.indices, dense_block=-1, device=None)
+    assert S.stats()["dense_rows"] == 0 and S.export_dense_rows().size == 0
+    with pytest.raises(KKTError) as ei:
+        KKTSolver(s.n, s.indptr, s.indices, dense_block=-2, device=None)
+    assert ei.value.status == _capi.KKT_ERR_ARG

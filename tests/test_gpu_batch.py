@@ -14,6 +14,7 @@ import torch
 import oracle
 from kktgen import config_sequence
 from paper_2306_14337_gb300 import KKTSolver
+from fill_split import on_fill
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -25,8 +26,9 @@ def _batch(s, k, B):
     return vals, bs
 
 
-def _check_factor(got, o, fp32):
+def _check_factor(S, got, o, fp32):
     rp, ci, ref, E = o.F.lu_csr()
+    got = on_fill(S, rp, ci, got)
     d = np.abs(got - ref)
     tol = np.maximum(1e-5 * np.abs(ref), 4 * E * 2.0 ** 29) if fp32 else np.maximum(1e-11 * np.abs(ref), 4 * E)
     assert np.all(d <= tol), int(np.sum(~(d <= tol)))
@@ -45,7 +47,7 @@ def test_batched_factors_and_refined_solves(fp32):
     S.batch_refactor(vt)
     for sc in (0, 17, 31, 32, 39):
         o = oracle.Oracle(s.n, s.indptr, s.indices, vals[:, sc], p, tau_rel=2.0 ** -24 if fp32 else 1e-14)
-        _check_factor(S.batch_export_factors(sc).cpu().numpy(), o, fp32)
+        _check_factor(S, S.batch_export_factors(sc).cpu().numpy(), o, fp32)
     x = S.batch_solve(bt)
     info = S.batch_refine(bt, x, tol=1e-14, max_it=40)
     xh = x.cpu().numpy()

