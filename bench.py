@@ -649,8 +649,10 @@ def run_native(args, ws, rank, local):
     t_ref = ph_ms["refactor"] * 1e-3
     by_ref = st["bytes_refactor"]
     achieved = by_ref / t_ref / 1e9
-    roof = {"bound": "hbm", "kernel": f"k_refactor<{'float' if wl['fp32'] else 'double'}> "
-                                      f"(+k_scale, k_amax, k_pack_tiles in the same events)",
+    tname = 'float' if wl['fp32'] else 'double'
+    roof = {"bound": "hbm", "kernel": f"k_refactor<{tname}>"
+                                      + (f" + k_dense_lu<{tname}>" if st["dense_rows"] else "")
+                                      + " (+k_scale, k_amax, k_pack_tiles in the same events)",
             "achieved": achieved, "peak": peak_hbm, "unit": "GB/s", "frac": achieved / peak_hbm,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
             "algorithmic_bytes_per_launch": by_ref,
@@ -667,7 +669,7 @@ def run_native(args, ws, rank, local):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": dname, "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "nnz": nnz, "nnz_lu": st["nnz_lu"],
-                   "levels": st["n_levels"], "value_sets": K,
+                   "levels": st["n_levels"], "value_sets": K, "dense_rows": st["dense_rows"],
                    "factors": "FP32, FP64 residual/refinement/pivot test" if wl["fp32"] else "FP64",
                    "refine": wl["refine"],
                    "l2": "flushed between timed steps (256 MiB write, outside the step events)",

@@ -137,6 +137,10 @@ typedef struct {
                                fill pattern of the oracle's definition are exactly
                                zero.  Used by kkt_refactor; the batched and queued
                                refactorizations treat the block's rows as sparse rows. */
+    int refactor_row_cap;   /* entries of the shared-memory row buffer of each warp of
+                               the single-system refactorization (0: the longest row,
+                               at most 1,024); longer rows work in global memory.  A
+                               larger buffer fits fewer warps on an SM. */
 } kkt_options;
 
 typedef struct {
@@ -166,6 +170,7 @@ typedef struct {
                                rows longer than 1,024 entries (0: no such rows) */
     int refactor_big_cap;   /* row capacity (entries) of those warps' shared memory */
     int dense_rows;         /* rows of the dense root block (0: none) */
+    int refactor_row_cap;   /* row buffer entries of the refactorization's warps */
 } kkt_stats;
 
 typedef struct {
@@ -358,7 +363,8 @@ kkt_status kkt_export_factors(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
  * phase 0 refactorization (work item = row, numbered like kkt_export_symbolic), 1 forward solve,
  * 2 backward solve, 3 transposed forward, 4 transposed backward (work item =
  * task in claim order, followed by the long tasks that ran on a CTA each, in
- * decreasing length).  out_host receives 2 words per item, the %globaltimer
+ * decreasing length), 5 the dense root block's LU (work item = tile task in
+ * claim order: per step the diagonal tile, the L and U tiles, the updates).  out_host receives 2 words per item, the %globaltimer
  * value (ns) at claim and at completion; *n_items the number of items copied.
  * Synchronizes the device.
  */

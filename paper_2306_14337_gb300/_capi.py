@@ -53,6 +53,7 @@ class Options(C.Structure):
         ("jacobi_sweeps", C.c_int),
         ("user_row_perm", C.POINTER(C.c_int)),
         ("dense_block", C.c_int),
+        ("refactor_row_cap", C.c_int),
     ]
 
 
@@ -83,6 +84,7 @@ class Stats(C.Structure):
         ("refactor_big_warps", C.c_int),
         ("refactor_big_cap", C.c_int),
         ("dense_rows", C.c_int),
+        ("refactor_row_cap", C.c_int),
     ]
 
 

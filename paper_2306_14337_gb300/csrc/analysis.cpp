@@ -266,7 +266,7 @@ static void etree_heights(int n, const std::vector<int> &grp, const std::vector<
 }
 
 int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
-            Analysis &out, std::string &err, long long map_budget_bytes, int dense_req) {
+            Analysis &out, std::string &err, long long map_budget_bytes, int dense_req, int dense_max) {
     int rc = validate_pattern(n, rp, ci);
     if (rc) { err = "malformed CSR pattern (n <= 0, unsorted, duplicate or out-of-range index)"; return rc; }
     if (rp[n] > (1 << 30)) { err = "too many entries"; return A_ERR_ARG; }
@@ -411,7 +411,7 @@ int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_p
             std::vector<int> lcol(n, 0);
             for (size_t q = 0; q < lci.size(); q++) lcol[lci[q]]++;
             long long cnt = 0;
-            const int tmax = std::min(n, DENSE_MAX_ROWS);
+            const int tmax = std::min({n, DENSE_MAX_ROWS, dense_max});
             for (int t = 1; t <= tmax; t++) {
                 cnt += lcol[n - t];
                 if ((double)(t + 2 * cnt) >= DENSE_MIN_DENSITY * (double)t * (double)t) s = t;

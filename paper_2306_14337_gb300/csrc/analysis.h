@@ -96,8 +96,9 @@ int max_product_matching(int n, const int *rp, const int *ci, const double *val,
 // trailing block of at most DENSE_MAX_ROWS rows whose pattern is at least
 // DENSE_MIN_DENSITY full, if it has DENSE_MIN_ROWS rows or more); k > 0
 // k rows.  Either is capped at the length of the path of the elimination
-// tree that ends the internal order.
+// tree that ends the internal order; the automatic choice also at dense_max.
 int analyze(int n, const int *rp, const int *ci, int ordering, const int *user_perm,
-            Analysis &out, std::string &err, long long map_budget_bytes = 0, int dense_req = -1);
+            Analysis &out, std::string &err, long long map_budget_bytes = 0, int dense_req = -1,
+            int dense_max = DENSE_MAX_ROWS);
 
 }  // namespace kkt

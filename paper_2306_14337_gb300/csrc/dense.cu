@@ -2,40 +2,35 @@
 //
 // The top of the elimination tree of the ACOPF KKT matrices is a chain of
 // separator rows whose trailing block of the combined L+U pattern is nearly
-// full (70,000-bus KKT: the last 768 rows completely, the last 1,000 to 87%).
-// Eliminated row by row, these rows are the end of the refactorization's
-// critical path: each waits for the row above it and then applies a pivot row
-// of up to a thousand entries.  Sec. 4 of arXiv 2306.14337 discusses the
-// supernodal alternative (dense blocks for groups of columns) and why it fails
-// on the small blocks of power-grid matrices; this block is not small.
+// full (70,000-bus KKT: the last 768 rows completely, the last 1,131 to 80%).
+// Eliminated row by row, these rows end the refactorization's critical path:
+// each waits for the row above it and then applies a pivot row of up to a
+// thousand entries.  Sec. 4 of arXiv 2306.14337 discusses the supernodal
+// alternative (dense blocks for groups of columns) and why it fails on the
+// small blocks of power-grid matrices; this block is not small.
 //
 // The analysis makes the trailing block of dense_rows rows a full square
 // block (explicit zeros).  The row kernel reduces each of its rows only by the
 // pivots below the block -- the Schur complement S = A'_TT - L_TB U_BT -- and
-// leaves it in a dense row-major array.  This kernel then factors S = L_TT U_TT
-// by a right-looking blocked LU without row exchanges (the fixed pivot
-// sequence, with the row kernel's FP64 perturbation test), panels of 32:
-//   1. every CTA that has panel work factors the 32 x 32 diagonal block
-//      itself (one warp, in registers; the arithmetic is identical in every
-//      CTA, so all get the same factors; CTA 0 writes them out and counts
-//      perturbed and negative pivots), then its warps solve 32-row groups of
-//      the L panel (X U_kk = A_ik, one row per lane) and 32-column groups of
-//      the U panel (L_kk Y = A_kj, one column per lane);
-//   2. grid barrier; the trailing block takes the rank-32 update in 64 x 64
-//      tiles (panel pieces staged in shared memory);
-//   3. grid barrier; next panel.
-// Every entry is reduced by its terms one at a time, in increasing pivot
-// order, a(i,j) <- a(i,j) - l(i,d) u(d,j), and a multiplier is the reduced
-// entry times the reciprocal pivot -- the row kernel's arithmetic; only the
-// grouping of the work differs.  Finally the block is copied into the
-// combined storage (its rows' tails) and the transposed copy.  The block
-// (at most 2,048^2 words) stays in L2, so every access bypasses L1 (.cg):
-// other SMs wrote it since the last barrier.
-//
-// The CTAs wait on each other at the barriers, so the kernel is launched
-// cooperatively (all CTAs resident at once; the launch fails otherwise).
-// Each barrier wait is bounded by spin_limit polls; on expiry it raises
-// KKT_ERR_TIMEOUT in the status word and the CTA goes on (results invalid).
+// leaves it in a dense row-major array.  This kernel factors S = L_TT U_TT
+// without row exchanges (the fixed pivot sequence, with the row kernel's
+// perturbation test) as a left-looking LU by block columns of CW columns:
+// CTA j keeps block column j of S in shared memory and, for every block
+// column k < j as soon as CTA k has published it,
+//   U(k,j) = L_kk^-1 S(k,j)                  (one thread per column)
+//   S(i,j) -= L(i,k) U(k,j) for the rows below (one thread per row),
+// then factors its own block: the diagonal tile (one warp, a lane per row,
+// the pivot tests) and the L part below it (X U_jj = S, a thread per row),
+// and publishes the block column (global memory, then a release flag).  The
+// CTAs wait on lower-numbered CTAs only, so they are launched cooperatively
+// (all resident at once, one per SM).  A chain of block columns is the
+// critical path; everything else overlaps it.  Every entry takes its terms
+// one at a time in increasing pivot order, a(i,j) <- a(i,j) - l(i,d) u(d,j),
+// and a multiplier is the reduced entry times the reciprocal pivot: the row
+// kernel's arithmetic, grouped differently.  Finally each CTA writes its block
+// column to the combined storage (the tails of the block's rows) and the
+// transposed copy.  Waits are bounded by spin_limit polls (KKT_ERR_TIMEOUT,
+// results invalid).
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -47,283 +42,335 @@ namespace kkt {
 namespace {
 
 constexpr unsigned DFULL = 0xffffffffu;
-constexpr int DNB = 32;                  // panel width
-constexpr int DTILE = 64;                // trailing-update tile edge
 constexpr int DWARPS = 8;
 constexpr int DTHREADS = DWARPS * 32;
+constexpr int DFLAG = 32;                // ints per published flag (one 128-byte line each)
 
-__device__ __forceinline__ unsigned dn_ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ int dn_ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ int dn_ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void dn_st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long dn_gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
-// Barrier over the grid.  The arrival counter only grows during a launch
-// (the host zeroes it before each launch): barrier k of a CTA waits until
-// k * gridDim.x arrivals, so a CTA whose wait ran out stays in step.
-__device__ __forceinline__ void dn_grid_barrier(const RunCfg &rc, unsigned &k) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned target = (++k) * gridDim.x;
-        atomicAdd(rc.dense_bar, 1u);
+// Thread 0 waits until flag *f is set (bounded), then the CTA's barrier.
+__device__ __forceinline__ void dn_wait_flag(const RunCfg &rc, const int *f) {
+    if (threadIdx.x == 0 && dn_ld_relaxed(f) == 0) {
         long long it = 0;
         unsigned ns = 32;
-        while (dn_ld_acquire(rc.dense_bar) < target) {
+        for (;;) {
             __nanosleep(ns);
+            if (dn_ld_relaxed(f) != 0) break;
             if (ns < 256) ns <<= 1;
-            if (++it > rc.spin_limit) {
+            if ((++it & 7) == 0 && dn_ld_relaxed(rc.status + ST_ABORT)) break;
+            if (it > rc.spin_limit) {
                 atomicExch(rc.status + ST_TIMEOUT, 1);
                 atomicExch(rc.status + ST_ABORT, 1);
                 break;
             }
         }
-        __threadfence();
     }
+    if (threadIdx.x == 0) (void)dn_ld_acquire(f);
     __syncthreads();
 }
 
-// Diagonal block [k0, k0 + kb)^2 of S, one warp, lane r = block row r.
-// Leaves L (strictly below) and U (on and above the diagonal) in sb and the
-// reciprocal pivots in srcp; the writer CTA also stores them to D, rcp and
-// the status words.
-template <typename T>
-__device__ __forceinline__ void dn_factor_diag(const DevPattern &P, const RunCfg &rc,
-                                               const double *__restrict__ aval, const double *__restrict__ sp,
-                                               T *D, int ld, int lo, int k0, int kb, double tau, T *rcp,
-                                               T (*sb)[DNB + 1], T *srcp, bool writer, int lane) {
-    T a[DNB];
-    const int R = k0 + lane;
-    const bool mine = lane < kb;
-#pragma unroll
-    for (int c = 0; c < DNB; c++) a[c] = (mine && c < kb) ? __ldcg(D + (size_t)R * ld + k0 + c) : T(0);
-    double aii = 0.0;                               // A'_ii: sign of a perturbed pivot
-    if (mine) {
-        const int i = lo + R;
-        const int k = P.src[P.diag[i]];
-        if (k >= 0) aii = sp[i] * sp[i] * aval[k];
+// The smallest float >= t (t >= 0): for a float p, |p| >= t exactly when
+// |p| >= dn_float_up(t), so the FP64 pivot test of an FP32 pivot needs no
+// FP64 arithmetic (FP64 instructions are slow on this GPU, and the tests of a
+// diagonal tile are sequential).
+__device__ __forceinline__ float dn_float_up(double t) { return __double2float_ru(t); }
+// !(|p| >= tau): the pivot is too small (or NaN)
+template <typename T> __device__ __forceinline__ bool dn_small(T p, double tau, float tau_up);
+template <> __device__ __forceinline__ bool dn_small<float>(float p, double, float tau_up) {
+    return !(fabsf(p) >= tau_up);
+}
+template <> __device__ __forceinline__ bool dn_small<double>(double p, double tau, float) {
+    return !(fabs(p) >= tau);
+}
+
+// 16-byte vectors of T (4 floats or 2 doubles)
+template <typename T> struct V16;
+template <> struct V16<float> {
+    using type = float4;
+    static constexpr int N = 4;
+    __device__ static float at(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+};
+template <> struct V16<double> {
+    using type = double2;
+    static constexpr int N = 2;
+    __device__ static double at(const double2 &v, int e) { return e == 0 ? v.x : v.y; }
+};
+
+// Shared memory of k_dense_lu<T, CW>: the block column col[s][CW + 1] (odd
+// pitch: threads on different rows hit different banks), two aligned tiles
+// tk / tu [CW][CW + 16 / sizeof(T)] (16-byte rows for broadcast vector reads)
+// and the reciprocal pivots.
+template <typename T, int CW> struct DnSmem {
+    static constexpr int CP = CW + 1;
+    static constexpr int TP = CW + 16 / (int)sizeof(T);
+    static size_t bytes(int s) {
+        const size_t colb = ((size_t)s * CP * sizeof(T) + 15) / 16 * 16;
+        return colb + 2 * (size_t)CW * TP * sizeof(T) + (size_t)CW * sizeof(T);
     }
+};
+
+template <typename T, int CW>
+__global__ void __launch_bounds__(DTHREADS, 1)
+k_dense_lu(DevPattern P, RunCfg rc, const double *__restrict__ aval, const double *__restrict__ sp, T *LU,
+           T *LUT, T *rcp, double tau_rel) {
+    using SM = DnSmem<T, CW>;
+    constexpr int CP = SM::CP, TP = SM::TP;
+    using VT = typename V16<T>::type;
+    constexpr int VN = V16<T>::N;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int lo = rc.dense_lo, s = P.n - lo, ld = rc.dense_ld;
+    T *D = reinterpret_cast<T *>(rc.dense);
+    int *flag = rc.dense_ctl;
+    T(*col)[CP] = reinterpret_cast<T(*)[CP]>(dsm);  // block column j: s rows
+    T(*tk)[TP] = reinterpret_cast<T(*)[TP]>(dsm + ((size_t)s * CP * sizeof(T) + 15) / 16 * 16);
+    T(*tu)[TP] = tk + CW;                           // U(k,j) rows / unused
+    T *srcp = reinterpret_cast<T *>(tu + CW);       // reciprocal pivots of block column j
+    const int j = blockIdx.x, c0 = j * CW, nc = min(CW, s - c0);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const double tau = tau_rel * __longlong_as_double((long long)rc.norms[NM_AMAX]);
+    const long long tbase = rc.trace_stride * TR_DENSE;
+    for (int e = tid; e < s * CW; e += DTHREADS) {
+        const int r = e / CW, c = e % CW;
+        col[r][c] = c < nc ? __ldcg(D + (size_t)r * ld + c0 + c) : T(0);
+    }
+    __syncthreads();
+    if (rc.trace != nullptr && tid == 0) rc.trace[tbase + 2LL * j] = dn_gtimer();
+    // left-looking: block columns k < j, in order
+    for (int k = 0; k < j; k++) {
+        const int k0 = k * CW;                      // a full block column (k0 + CW <= c0)
+        dn_wait_flag(rc, flag + (size_t)k * DFLAG);
+        for (int e = tid; e < CW * CW; e += DTHREADS) {
+            const int r = e / CW, c = e % CW;
+            tk[r][c] = __ldcg(D + (size_t)(k0 + r) * ld + k0 + c);
+        }
+        __syncthreads();
+        if (tid < CW) {                             // U(k,j) = L_kk^-1 S(k,j): a column per thread
+            T y[CW];
 #pragma unroll
-    for (int p = 0; p < DNB; p++) {
-        if (p < kb) {
-            T r = T(0);
-            if (lane == p) {                        // pivot test in FP64
-                double pv = (double)a[p];
-                if (!(fabs(pv) >= tau) || isinf(pv)) {
-                    if (writer) {
+            for (int r = 0; r < CW; r++) y[r] = col[k0 + r][tid];
+#pragma unroll
+            for (int r = 1; r < CW; r++)
+#pragma unroll
+                for (int q = 0; q < CW; q++)
+                    if (q < r) y[r] = y[r] - tk[r][q] * y[q];
+#pragma unroll
+            for (int r = 0; r < CW; r++) {
+                col[k0 + r][tid] = y[r];
+                tu[r][tid] = y[r];                  // columns >= nc stay zero
+            }
+        }
+        __syncthreads();
+        // the rows below: S(R, j) -= L(R, k) U(k, j), a row per thread, the
+        // row's CW entries in registers, U rows read as broadcast vectors
+        for (int R = k0 + CW + tid; R < s; R += DTHREADS) {
+            T l[CW], acc[CW];
+            const VT *lp = reinterpret_cast<const VT *>(D + (size_t)R * ld + k0);
+#pragma unroll
+            for (int q = 0; q < CW / VN; q++) {
+                const VT v = __ldcg(lp + q);
+#pragma unroll
+                for (int e = 0; e < VN; e++) l[q * VN + e] = V16<T>::at(v, e);
+            }
+#pragma unroll
+            for (int c = 0; c < CW; c++) acc[c] = col[R][c];
+#pragma unroll
+            for (int q = 0; q < CW; q++) {
+#pragma unroll
+                for (int c4 = 0; c4 < CW / VN; c4++) {
+                    const VT u = *reinterpret_cast<const VT *>(&tu[q][c4 * VN]);
+#pragma unroll
+                    for (int e = 0; e < VN; e++) acc[c4 * VN + e] = acc[c4 * VN + e] - l[q] * V16<T>::at(u, e);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CW; c++) col[R][c] = acc[c];
+        }
+        __syncthreads();
+    }
+    // own diagonal tile: warp 0, lane r = row c0 + r
+    if (wid == 0) {
+        const T tau_t = (T)tau;                     // a perturbed pivot: +-tau rounded to T
+        const float tau_up = dn_float_up(tau);
+        const bool mine = lane < nc;
+        T a[CW];
+#pragma unroll
+        for (int c = 0; c < CW; c++) a[c] = (mine && c < nc) ? col[c0 + lane][c] : T(0);
+        double aii = 0.0;                           // A'_ii: sign of a perturbed pivot
+        if (mine) {
+            const int i = lo + c0 + lane;
+            const int e = P.src[P.diag[i]];
+            if (e >= 0) aii = sp[i] * sp[i] * aval[e];
+        }
+#pragma unroll
+        for (int p = 0; p < CW; p++) {
+            if (p < nc) {
+                T r = T(0);
+                if (lane == p) {
+                    T pv = a[p];
+                    if (dn_small<T>(pv, tau, tau_up) || isinf(pv)) {
                         if (!isfinite(pv)) atomicExch(rc.status + ST_NONFINITE, 1);
                         atomicAdd(rc.status + ST_PERTURBED, 1);
                         atomicAdd(rc.status + ST_PERT_LAST, 1);
+                        pv = (aii < 0.0) ? -tau_t : tau_t;
                     }
-                    pv = (aii < 0.0) ? -tau : tau;
+                    if (pv < T(0)) atomicAdd(rc.status + ST_NEGATIVE, 1);
+                    a[p] = pv;
+                    r = T(1) / pv;
+                    srcp[p] = r;
+                    rcp[lo + c0 + p] = r;
                 }
-                if (writer && pv < 0.0) atomicAdd(rc.status + ST_NEGATIVE, 1);
-                a[p] = (T)pv;
-                r = T(1) / a[p];
-                srcp[p] = r;
-                if (writer) rcp[lo + R] = r;
-            }
-            r = __shfl_sync(DFULL, r, p);
-            const T l = a[p] * r;                   // rows below p: the multiplier
+                r = __shfl_sync(DFULL, r, p);
+                const T l = a[p] * r;               // rows below p: the multiplier
 #pragma unroll
-            for (int c = 0; c < DNB; c++) {
-                if (c > p) {
-                    const T u = __shfl_sync(DFULL, a[c], p);
-                    if (lane > p) a[c] = a[c] - l * u;
+                for (int c = 0; c < CW; c++) {
+                    if (c > p) {
+                        const T u = __shfl_sync(DFULL, a[c], p);
+                        if (lane > p) a[c] = a[c] - l * u;
+                    }
                 }
+                if (lane > p) a[p] = l;
             }
-            if (lane > p) a[p] = l;
         }
-    }
+        if (lane < CW) {
 #pragma unroll
-    for (int c = 0; c < DNB; c++) sb[lane][c] = a[c];
-    if (writer && mine) {
-#pragma unroll
-        for (int c = 0; c < DNB; c++)
-            if (c < kb) __stcg(D + (size_t)R * ld + k0 + c, a[c]);
-    }
-}
-
-// L panel: rows R = r0 + 32 g + lane, X U_kk = S(R, k0:k0+kb).
-template <typename T>
-__device__ __forceinline__ void dn_panel_l(T *D, int ld, int s, int k0, int kb, int R,
-                                           const T (*sb)[DNB + 1], const T *srcp) {
-    T x[DNB];
-    const bool ok = R < s;
-#pragma unroll
-    for (int c = 0; c < DNB; c++) x[c] = (ok && c < kb) ? __ldcg(D + (size_t)R * ld + k0 + c) : T(0);
-#pragma unroll
-    for (int c = 0; c < DNB; c++) {
-        if (c < kb) {
-            x[c] = x[c] * srcp[c];
-#pragma unroll
-            for (int c2 = 0; c2 < DNB; c2++)
-                if (c2 > c) x[c2] = x[c2] - x[c] * sb[c][c2];
+            for (int c = 0; c < CW; c++) {
+                if (mine) col[c0 + lane][c] = a[c];
+                tk[lane][c] = a[c];                 // U_jj (and L_jj) in the aligned tile
+            }
         }
-    }
-    if (ok) {
-#pragma unroll
-        for (int c = 0; c < DNB; c++)
-            if (c < kb) __stcg(D + (size_t)R * ld + k0 + c, x[c]);
-    }
-}
-
-// U panel: columns C = r0 + 32 g + lane, L_kk Y = S(k0:k0+kb, C).
-template <typename T>
-__device__ __forceinline__ void dn_panel_u(T *D, int ld, int s, int k0, int kb, int C,
-                                           const T (*sb)[DNB + 1]) {
-    T y[DNB];
-    const bool ok = C < s;
-#pragma unroll
-    for (int r = 0; r < DNB; r++) y[r] = (ok && r < kb) ? __ldcg(D + (size_t)(k0 + r) * ld + C) : T(0);
-#pragma unroll
-    for (int r = 0; r < DNB; r++) {
-        if (r < kb) {
-#pragma unroll
-            for (int r2 = 0; r2 < DNB; r2++)
-                if (r2 > r) y[r2] = y[r2] - sb[r2][r] * y[r];
-        }
-    }
-    if (ok) {
-#pragma unroll
-        for (int r = 0; r < DNB; r++)
-            if (r < kb) __stcg(D + (size_t)(k0 + r) * ld + C, y[r]);
-    }
-}
-
-// Rank-kb update of one 64 x 64 tile of the trailing block at (R0, C0).
-template <typename T>
-__device__ __forceinline__ void dn_update_tile(T *D, int ld, int s, int k0, int kb, int R0, int C0,
-                                               T (*sl)[DNB + 1], T (*su)[DTILE + 1]) {
-    const int tid = threadIdx.x;
-    for (int e = tid; e < DTILE * DNB; e += DTHREADS) {
-        const int r = e / DNB, k = e % DNB;
-        const int R = R0 + r;
-        sl[r][k] = (R < s && k < kb) ? __ldcg(D + (size_t)R * ld + k0 + k) : T(0);
-    }
-    for (int e = tid; e < DNB * DTILE; e += DTHREADS) {
-        const int k = e / DTILE, c = e % DTILE;
-        const int C = C0 + c;
-        su[k][c] = (k < kb && C < s) ? __ldcg(D + (size_t)(k0 + k) * ld + C) : T(0);
     }
     __syncthreads();
-    const int ty = tid >> 4, tx = tid & 15;
-    T acc[4][4];
+    // L part below the diagonal tile: X U_jj = S, a row per thread
+    for (int R = c0 + CW + tid; R < s; R += DTHREADS) {
+        T x[CW];
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+        for (int c = 0; c < CW; c++) x[c] = col[R][c];
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int R = R0 + ty + 16 * i, C = C0 + tx + 16 * j;
-            acc[i][j] = (R < s && C < s) ? __ldcg(D + (size_t)R * ld + C) : T(0);
+        for (int c = 0; c < CW; c++) {
+            x[c] = x[c] * srcp[c];
+#pragma unroll
+            for (int c4 = 0; c4 < CW / VN; c4++) {
+                if ((c4 + 1) * VN - 1 > c) {
+                    const VT u = *reinterpret_cast<const VT *>(&tk[c][c4 * VN]);
+#pragma unroll
+                    for (int e = 0; e < VN; e++)
+                        if (c4 * VN + e > c) x[c4 * VN + e] = x[c4 * VN + e] - x[c] * V16<T>::at(u, e);
+                }
+            }
         }
-    for (int k = 0; k < kb; k++) {
-        T lv[4], uv[4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) lv[i] = sl[ty + 16 * i][k];
-#pragma unroll
-        for (int j = 0; j < 4; j++) uv[j] = su[k][tx + 16 * j];
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int j = 0; j < 4; j++) acc[i][j] = acc[i][j] - lv[i] * uv[j];
+        for (int c = 0; c < CW; c++) col[R][c] = x[c];
     }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int R = R0 + ty + 16 * i, C = C0 + tx + 16 * j;
-            if (R < s && C < s) __stcg(D + (size_t)R * ld + C, acc[i][j]);
-        }
-    __syncthreads();                                // the tiles are reused by the next one
+    __syncthreads();
+    // publish rows >= c0 of the block column (the L part and the diagonal tile)
+    for (int e = tid; e < (s - c0) * CW; e += DTHREADS) {
+        const int r = c0 + e / CW, c = e % CW;
+        if (c < nc) __stcg(D + (size_t)r * ld + c0 + c, col[r][c]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        dn_st_release(flag + (size_t)j * DFLAG, 1);
+        if (rc.trace != nullptr) rc.trace[tbase + 2LL * j + 1] = dn_gtimer();
+    }
+    // final values: the combined storage (row tails) and the transposed copy
+    for (int e = tid; e < s * CW; e += DTHREADS) {
+        const int r = e / CW, c = e % CW;
+        if (c < nc) LU[__ldg(P.lu_rp + lo + r + 1) - s + c0 + c] = col[r][c];
+    }
+    for (int e = tid; e < s * CW; e += DTHREADS) {
+        const int c = e / s, r = e % s;
+        if (c < nc) LUT[__ldg(P.lu_rp + lo + c0 + c + 1) - s + r] = col[r][c];
+    }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(DTHREADS, 1)
-k_dense_lu(DevPattern P, RunCfg rc, const double *__restrict__ aval, const double *__restrict__ sp,
-           T *LU, T *LUT, T *rcp, double tau_rel) {
-    __shared__ T sb[DNB][DNB + 1];
-    __shared__ T srcp[DNB];
-    __shared__ T sl[DTILE][DNB + 1];
-    __shared__ T su[DNB][DTILE + 1];
-    const int lo = rc.dense_lo, s = P.n - lo, ld = rc.dense_ld;
-    T *D = reinterpret_cast<T *>(rc.dense);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const double tau = tau_rel * __longlong_as_double((long long)rc.norms[NM_AMAX]);
-    const long long ss = (long long)s * s;
-    const long long gthreads = (long long)gridDim.x * DTHREADS;
-    unsigned bk = 0;
-    if (rc.symmetric) {            // LDL^T rows reduced only their upper part: mirror it
-        for (long long e = (long long)blockIdx.x * DTHREADS + threadIdx.x; e < ss; e += gthreads) {
-            const int r = (int)(e / s), c = (int)(e % s);
-            if (r > c) __stcg(D + (size_t)r * ld + c, __ldcg(D + (size_t)c * ld + r));
-        }
-        dn_grid_barrier(rc, bk);
-    }
-    for (int k0 = 0; k0 < s; k0 += DNB) {
-        const int kb = min(DNB, s - k0);
-        const int r0 = k0 + kb, rest = s - r0;
-        const int ngrp = (rest + 31) >> 5;
-        const int items = 2 * ngrp;                 // L groups, then U groups
-        if (blockIdx.x == 0 || (int)blockIdx.x * DWARPS < items) {
-            if (wid == 0)
-                dn_factor_diag<T>(P, rc, aval, sp, D, ld, lo, k0, kb, tau, rcp, sb, srcp, blockIdx.x == 0, lane);
-            __syncthreads();
-            const int item = (int)blockIdx.x * DWARPS + wid;
-            if (item < ngrp)
-                dn_panel_l<T>(D, ld, s, k0, kb, r0 + 32 * item + lane, sb, srcp);
-            else if (item < items)
-                dn_panel_u<T>(D, ld, s, k0, kb, r0 + 32 * (item - ngrp) + lane, sb);
-        }
-        dn_grid_barrier(rc, bk);
-        if (rest > 0) {
-            const int nt = (rest + DTILE - 1) / DTILE;
-            for (int t = blockIdx.x; t < nt * nt; t += gridDim.x)
-                dn_update_tile<T>(D, ld, s, k0, kb, r0 + (t / nt) * DTILE, r0 + (t % nt) * DTILE, sl, su);
-            dn_grid_barrier(rc, bk);
-        }
-    }
-    // the block's rows are the tails of rows lo .. n-1 of the combined storage;
-    // entry (r, c) of the block is entry (c, r) of the transposed copy
-    for (long long e = (long long)blockIdx.x * DTHREADS + threadIdx.x; e < ss; e += gthreads) {
-        const int r = (int)(e / s), c = (int)(e % s);
-        const T v = __ldcg(D + (size_t)r * ld + c);
-        LU[(long long)P.lu_rp[lo + r + 1] - s + c] = v;
-        LUT[(long long)P.lu_rp[lo + c + 1] - s + r] = v;
-    }
-}
+template <typename T, int CW> size_t dn_smem(int s) { return DnSmem<T, CW>::bytes(s); }
+
+// block-column width of a block of s rows: 32 while a block column fits in
+// shared memory, else 16
+template <typename T> int dn_width(int s) { return dn_smem<T, 32>(s) <= 200 * 1024 ? 32 : 16; }
 
 }  // namespace
 
 int dense_lu_threads() { return DTHREADS; }
 
+size_t dense_lu_ctl_bytes(int s) { return (size_t)((s + 15) / 16) * DFLAG * sizeof(int); }
+
+int dense_lu_max_rows(int fp32) {
+    // the largest block whose 16-column block columns fit in shared memory
+    int m = 16;
+    while (m < 4096 && (fp32 ? dn_smem<float, 16>(m + 16) : dn_smem<double, 16>(m + 16)) <= 200 * 1024) m += 16;
+    return m;
+}
+
+// Set the kernel's shared-memory limit for a block of s rows and check that
+// all of its CTAs (one per block column) fit on the device at once.
+cudaError_t dense_lu_prepare(int fp32, int s, int sms, int *ctas) {
+    const void *fn;
+    size_t smem;
+    int cw;
+    if (fp32) {
+        cw = dn_width<float>(s);
+        fn = cw == 32 ? (const void *)k_dense_lu<float, 32> : (const void *)k_dense_lu<float, 16>;
+        smem = cw == 32 ? dn_smem<float, 32>(s) : dn_smem<float, 16>(s);
+    } else {
+        cw = 16;
+        fn = (const void *)k_dense_lu<double, 16>;
+        smem = dn_smem<double, 16>(s);
+    }
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, DTHREADS, smem);
+    if (e != cudaSuccess) return e;
+    *ctas = (s + cw - 1) / cw;
+    if ((long long)per * sms < *ctas) return cudaErrorCooperativeLaunchTooLarge;
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_dense_lu(const DevPattern &P, const RunCfg &rc, const double *aval, const double *sp,
-                            T *LU, T *LUT, T *rcp, double tau_rel, int grid, cudaStream_t stream) {
-    cudaError_t e = cudaMemsetAsync(rc.dense_bar, 0, sizeof(unsigned), stream);
+                            T *LU, T *LUT, T *rcp, double tau_rel, cudaStream_t stream) {
+    const int s = P.n - rc.dense_lo;
+    const int cw = sizeof(T) == 4 ? dn_width<T>(s) : 16;
+    cudaError_t e = cudaMemsetAsync(rc.dense_ctl, 0, dense_lu_ctl_bytes(s), stream);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
+    cfg.gridDim = dim3((unsigned)((s + cw - 1) / cw));
     cfg.blockDim = dim3(DTHREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = cw == 32 ? dn_smem<T, 32>(s) : dn_smem<T, 16>(s);   // host arithmetic only
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_dense_lu<T>, P, rc, aval, sp, LU, LUT, rcp, tau_rel);
+    if constexpr (sizeof(T) == 4) {
+        if (cw == 32) return cudaLaunchKernelEx(&cfg, k_dense_lu<T, 32>, P, rc, aval, sp, LU, LUT, rcp, tau_rel);
+    }
+    return cudaLaunchKernelEx(&cfg, k_dense_lu<T, 16>, P, rc, aval, sp, LU, LUT, rcp, tau_rel);
 }
 
 template cudaError_t launch_dense_lu<float>(const DevPattern &, const RunCfg &, const double *, const double *,
-                                            float *, float *, float *, double, int, cudaStream_t);
+                                            float *, float *, float *, double, cudaStream_t);
 template cudaError_t launch_dense_lu<double>(const DevPattern &, const RunCfg &, const double *, const double *,
-                                             double *, double *, double *, double, int, cudaStream_t);
-
-// CTAs of k_dense_lu<T> that fit on one SM at once (for the cooperative grid).
-cudaError_t dense_lu_per_sm(int fp32, int *per_sm) {
-    if (fp32)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_dense_lu<float>, DTHREADS, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_dense_lu<double>, DTHREADS, 0);
-}
+                                             double *, double *, double *, double, cudaStream_t);
 
 }  // namespace kkt

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 namespace kkt {
 
@@ -58,7 +59,7 @@ struct DevPattern {
     // longer than the small per-warp buffer (order_long), and the other rows
     // (order_rest), of n_free / n_long / n - n_free - n_long rows.
     const int *order_free, *order_long, *order_rest;
-    int n_free, n_long;
+    int n_free, n_long, n_rest;
     const unsigned *upd_off;             // update maps (null when not built)
     const unsigned short *upd_map;
     // First row of the dense root block (n: none).  The update maps hold no
@@ -127,24 +128,30 @@ struct RunCfg {
     int dense_lo;
     int dense_ld;
     void *dense;
-    unsigned *dense_bar;         // grid barrier of k_dense_lu: {arrivals, generation}
+    int *dense_ctl;              // k_dense_lu: one published flag per block column
 };
 
-// Launch k_dense_lu<T> (csrc/dense.cu) on `grid` co-resident CTAs: the
-// blocked LU of the dense root block left in rc.dense by the refactorization,
-// with the FP64 pivot test, then the block's factors written to LU (and its
-// transposed copy LUT) and its reciprocal pivots to rcp.
+// Launch k_dense_lu<T> (csrc/dense.cu): the LU of the dense root block left
+// in rc.dense by the refactorization, with the pivot test; the block's factors
+// go to LU (and the transposed copy LUT), its reciprocal pivots to rcp.
+// dense_lu_prepare (once per context) sets the kernel's shared-memory limit
+// for a block of s rows and returns its CTA count, or an error if they do not
+// all fit on the device at once; dense_lu_max_rows is the largest block it
+// takes; dense_lu_ctl_bytes the size of rc.dense_ctl.
 template <typename T>
 cudaError_t launch_dense_lu(const DevPattern &P, const RunCfg &rc, const double *aval, const double *sp,
-                            T *LU, T *LUT, T *rcp, double tau_rel, int grid, cudaStream_t stream);
+                            T *LU, T *LUT, T *rcp, double tau_rel, cudaStream_t stream);
 int dense_lu_threads();
-cudaError_t dense_lu_per_sm(int fp32, int *per_sm);
+int dense_lu_max_rows(int fp32);
+size_t dense_lu_ctl_bytes(int s);
+cudaError_t dense_lu_prepare(int fp32, int s, int sms, int *ctas);
 
 // Record the text returned by kkt_last_error() on the calling thread (every
 // translation unit of the library reports through this one store).
 void set_last_error(const std::string &msg);
 
 // Trace regions, one per phase, each (max work items) x 2 words.
-enum TracePhase { TR_REFACTOR = 0, TR_FWD = 1, TR_BWD = 2, TR_TFWD = 3, TR_TBWD = 4, TR_PHASES = 5 };
+// TR_DENSE: the block columns of k_dense_lu (start of its own work, publication).
+enum TracePhase { TR_REFACTOR = 0, TR_FWD = 1, TR_BWD = 2, TR_TFWD = 3, TR_TBWD = 4, TR_DENSE = 5, TR_PHASES = 6 };
 
 }  // namespace kkt

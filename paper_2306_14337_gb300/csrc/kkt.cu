@@ -948,10 +948,13 @@ __device__ __forceinline__ void refactor_row_sym(const DevPattern &P, const RunC
         cp_async_wait<0>();
         __syncwarp();
     }
-    if (dense) {                       // the block row's upper part; k_dense_lu mirrors it
+    if (dense) {                       // the block row's upper part, and by symmetry its column
         const int r = i - rc.dense_lo;
-        T *D = reinterpret_cast<T *>(rc.dense) + (size_t)r * rc.dense_ld + r;
-        for (int t = lane; t < ulen; t += 32) D[t] = w[t];
+        T *D = reinterpret_cast<T *>(rc.dense);
+        for (int t = lane; t < ulen; t += 32) {
+            D[(size_t)r * rc.dense_ld + r + t] = w[t];
+            D[(size_t)(r + t) * rc.dense_ld + r] = w[t];
+        }
         for (int t = lane; t < nst; t += 32) LUT[P.tpos[rb + t]] = LU[rb + t];
         return;
     }
@@ -1034,7 +1037,7 @@ k_refactor(DevPattern P, RunCfg rc, const double *__restrict__ aval, const doubl
     };
     drain(&rc.sched->next, P.order_free, P.n_free);
     if (big) drain(&rc.sched->next_long, P.order_long, P.n_long);
-    drain(&rc.sched->next_rest, P.order_rest, P.n - P.n_free - P.n_long);
+    drain(&rc.sched->next_rest, P.order_rest, P.n_rest);
     if (lane == 0) finish_launch(rc, e);
 }
 
@@ -2349,8 +2352,9 @@ struct kkt_ctx {
     double *d_qvec = nullptr;        // 2 n: Q b, and Q lambda
     double *d_qdA = nullptr;         // gradient on the entries of Q A (nnz)
     void *d_dense = nullptr;         // dense root block (dense_rows x dense_ld words)
-    unsigned *d_dense_bar = nullptr; // grid barrier of k_dense_lu
-    int dense_ld = 0, dense_grid = 0;
+    int *d_dense_ctl = nullptr;      // k_dense_lu: a published flag per block column
+    int dense_ld = 0, dense_grid = 0;   // dense_grid: CTAs (block columns) of k_dense_lu
+    int cap_r = 0;                   // row capacity of k_refactor's small warps
     bool factored = false;
     int last_iters = 0;
     double last_omega = -1.0;
@@ -2445,6 +2449,7 @@ void kkt_default_options(kkt_options *o) {
     o->jacobi_sweeps = 8;
     o->user_row_perm = nullptr;
     o->dense_block = 0;
+    o->refactor_row_cap = 0;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -2485,10 +2490,16 @@ static kkt_status upload(kkt_ctx *c) {
     // rows longer than the small per-warp buffer go to the big warps; rows
     // with no such row below them in the elimination tree come first
     const int cap_s = std::min(((std::max(a.max_row, 32) + 31) / 32) * 32, 1024);
+    // the single-system refactorization's per-warp row capacity (an option)
+    const int cap_r = c->opt.refactor_row_cap > 0
+                          ? std::min(((std::max(c->opt.refactor_row_cap, 32) + 31) / 32) * 32,
+                                     ((std::max(a.max_row, 32) + 31) / 32) * 32)
+                          : cap_s;
+    c->cap_r = cap_r;
     std::vector<int> ord_free, ord_long, ord_rest;
     {
         std::vector<char> is_long(n), below(n, 0);      // below: a long row in the subtree, excluding itself
-        for (int r = 0; r < n; r++) is_long[r] = a.lu_rp[r + 1] - a.lu_rp[r] > cap_s;
+        for (int r = 0; r < n; r++) is_long[r] = a.lu_rp[r + 1] - a.lu_rp[r] > cap_r;
         for (int r = 0; r < n; r++)                      // children before parents (postorder labels)
             if (a.parent[r] >= 0 && (below[r] || is_long[r])) below[a.parent[r]] = 1;
         ord_free.reserve(n);
@@ -2525,6 +2536,7 @@ static kkt_status upload(kkt_ctx *c) {
     c->P.nnz_a = nnza;
     c->P.n_free = (int)ord_free.size();
     c->P.n_long = (int)ord_long.size();
+    c->P.n_rest = (int)ord_rest.size();
     c->P.dense_lo = n - a.dense_rows;
 
     const bool f32 = c->opt.factor_fp32 != 0;
@@ -2581,18 +2593,18 @@ static kkt_status upload(kkt_ctx *c) {
             return vb + (staged ? ring : (mapped ? 0 : cb));
         };
         const size_t cta_max = 227 * 1024;
-        int nbig = 0, cap_big = cap;
+        int nbig = 0, cap_big = cap_r;
         if (!ord_long.empty() && nw >= 2 && c->opt.refactor_big_warps > 0) {
             cap_big = ((a.max_row + 31) / 32) * 32;
-            while (cap_big > cap && warp_bytes(cap_big) + (size_t)(nw - 1) * warp_bytes(cap) > cta_max)
+            while (cap_big > cap_r && warp_bytes(cap_big) + (size_t)(nw - 1) * warp_bytes(cap_r) > cta_max)
                 cap_big -= 32;
-            if (cap_big > cap) {
-                const long long each = (long long)warp_bytes(cap_big) - (long long)warp_bytes(cap);
-                const long long most = ((long long)cta_max - (long long)nw * (long long)warp_bytes(cap)) / each;
+            if (cap_big > cap_r) {
+                const long long each = (long long)warp_bytes(cap_big) - (long long)warp_bytes(cap_r);
+                const long long most = ((long long)cta_max - (long long)nw * (long long)warp_bytes(cap_r)) / each;
                 nbig = (int)std::max(1LL, std::min<long long>({(long long)c->opt.refactor_big_warps,
                                                                (long long)nw / 2, most}));
             } else {
-                cap_big = cap;
+                cap_big = cap_r;
             }
         }
         if (nbig == 0 && c->P.n_long > 0) {
@@ -2600,6 +2612,7 @@ static kkt_status upload(kkt_ctx *c) {
             c->P.order_free = c->P.order_f;
             c->P.n_free = n;
             c->P.n_long = 0;
+            c->P.n_rest = 0;
         }
         c->rc.nbig = nbig;
         c->rc.cap_big = cap_big;
@@ -2607,8 +2620,8 @@ static kkt_status upload(kkt_ctx *c) {
         c->rc.staged = staged ? 1 : 0;
         c->rc.symmetric = (staged && c->opt.symmetric) ? 1 : 0;   // LDL^T needs the update maps
         c->rc.warp_bytes_big = (int)warp_bytes(cap_big);
-        c->rc.warp_bytes_small = (int)warp_bytes(cap);
-        c->rsmem = (size_t)nbig * warp_bytes(cap_big) + (size_t)(nw - nbig) * warp_bytes(cap);
+        c->rc.warp_bytes_small = (int)warp_bytes(cap_r);
+        c->rsmem = (size_t)nbig * warp_bytes(cap_big) + (size_t)(nw - nbig) * warp_bytes(cap_r);
         int per_sm_r = 0;
         if (f32) {
             CK(ensure_smem((const void *)k_refactor<float>, c->rsmem));
@@ -2989,19 +3002,17 @@ static kkt_status upload(kkt_ctx *c) {
     c->rc.dense_lo = INT_MAX;
     c->rc.dense_ld = 0;
     c->rc.dense = nullptr;
-    c->rc.dense_bar = nullptr;
+    c->rc.dense_ctl = nullptr;
     if (a.dense_rows > 0) {
         const int sd = a.dense_rows;
         c->dense_ld = (sd + 31) / 32 * 32;
         const size_t db = (size_t)sd * c->dense_ld * tsz;
+        const size_t cb = dense_lu_ctl_bytes(sd);
         CK(cudaMalloc(&c->d_dense, db));
-        CK(cudaMalloc(&c->d_dense_bar, 256));
-        CK(cudaMemset(c->d_dense_bar, 0, 256));
-        c->device_bytes += db + 256;
-        int per = 0;
-        CK(dense_lu_per_sm(f32 ? 1 : 0, &per));
-        if (per < 1) { g_last_error = "dense block kernel does not fit on an SM"; return KKT_ERR_CUDA; }
-        c->dense_grid = sms;             // one CTA per SM, all resident (cooperative launch)
+        CK(cudaMalloc(&c->d_dense_ctl, cb));
+        CK(cudaMemset(c->d_dense_ctl, 0, cb));
+        c->device_bytes += db + cb;
+        CK(dense_lu_prepare(f32 ? 1 : 0, sd, sms, &c->dense_grid));
     }
     if (c->rowperm) {
         const size_t nnz = c->qmap.size();
@@ -3054,7 +3065,7 @@ void kkt_destroy(kkt_ctx *c) {
         cudaFreeHost(c->hb_norms);
         cudaFree(c->d_scratch);
         cudaFree(c->d_dense);
-        cudaFree(c->d_dense_bar);
+        cudaFree(c->d_dense_ctl);
         cudaFreeHost(c->h_norms);
     }
     delete c;
@@ -3072,7 +3083,7 @@ static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, con
     if (opt) c->opt = *opt; else kkt_default_options(&c->opt);
     if (c->opt.fgmres_restart < 1 || c->opt.max_refine < 0 || c->opt.spin_limit < 1 ||
         c->opt.refine_mode < KKT_REFINE_CLASSIC || c->opt.refine_mode > KKT_REFINE_FGMRES_JACOBI ||
-        c->opt.jacobi_sweeps < 0 || c->opt.dense_block < -1 ||
+        c->opt.jacobi_sweeps < 0 || c->opt.dense_block < -1 || c->opt.refactor_row_cap < 0 ||
         c->opt.max_batch < 1 || c->opt.cta_warps < 0 || c->opt.refactor_ctas < 0 ||
         c->opt.solve_ctas < 0) {
         g_last_error = "invalid option";
@@ -3133,7 +3144,15 @@ static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, con
             rp = qa_rp.data();
             ci = qa_ci.data();
         }
-        rc = analyze(n, rp, ci, c->opt.ordering, c->opt.user_perm, c->an, err, budget, c->opt.dense_block);
+        // The dense root block pays with FP32 factors (FP64 arithmetic is slow on
+        // this GPU: the block's FP64 LU is not faster than its rows' own chain),
+        // so the automatic choice applies to FP32 factors only; a requested block
+        // is capped at what k_dense_lu holds in shared memory.
+        int dreq = c->opt.dense_block;
+        if (dreq == 0 && !c->opt.factor_fp32) dreq = -1;
+        if (dreq > 0) dreq = std::min(dreq, dense_lu_max_rows(c->opt.factor_fp32 ? 1 : 0));
+        rc = analyze(n, rp, ci, c->opt.ordering, c->opt.user_perm, c->an, err, budget, dreq,
+                     dense_lu_max_rows(c->opt.factor_fp32 ? 1 : 0));
     } catch (const std::bad_alloc &) {
         g_last_error = "host allocation failed during analysis";
         return KKT_ERR_ALLOC;
@@ -3204,11 +3223,12 @@ template <typename T> static kkt_status launch_refactor(kkt_ctx *c, cudaStream_t
     CK(cudaMemsetAsync(c->d_lu, 0xff, (size_t)c->nnz_lu * sizeof(T), s));
     CK(cudaMemsetAsync(c->d_rcp, 0xff, (size_t)c->an.n * sizeof(T), s));
     RunCfg rc = c->rc;
+    rc.cap = c->cap_r;
     if (c->an.dense_rows > 0) {          // rows of the dense root block stop below it
         rc.dense_lo = c->an.n - c->an.dense_rows;
         rc.dense_ld = c->dense_ld;
         rc.dense = c->d_dense;
-        rc.dense_bar = c->d_dense_bar;
+        rc.dense_ctl = c->d_dense_ctl;
     }
     k_refactor<T><<<c->rgrid, c->cta_warps * 32, c->rsmem, s>>>(c->P, rc, c->values, c->d_sp,
                                                                (T *)c->d_lu, (T *)c->d_lut,
@@ -3217,7 +3237,7 @@ template <typename T> static kkt_status launch_refactor(kkt_ctx *c, cudaStream_t
     c->launches++;
     if (c->an.dense_rows > 0) {
         CK(launch_dense_lu<T>(c->P, rc, c->values, c->d_sp, (T *)c->d_lu, (T *)c->d_lut, (T *)c->d_rcp,
-                              c->tau_rel, c->dense_grid, s));
+                              c->tau_rel, s));
         c->launches++;
     }
     return pack_tiles<T>(c, s);
@@ -4395,6 +4415,7 @@ kkt_status kkt_get_stats(const kkt_ctx *c, kkt_stats *o) {
     o->n_tasks = (int)a.task_lo.size();
     o->max_task = a.max_task;
     o->dense_rows = a.dense_rows;
+    o->refactor_row_cap = c->cap_r;
     return KKT_OK;
 }
 
@@ -4599,7 +4620,7 @@ kkt_status kkt_export_trace(kkt_ctx *c, int phase, unsigned long long *out_host,
     if (!out_host || phase < 0 || phase >= TR_PHASES || max_items < 0) return KKT_ERR_ARG;
     if (!c->d_trace) { g_last_error = "tracing was not enabled at analysis"; return KKT_ERR_STATE; }
     DeviceGuard g(c->dev);
-    const long long items = phase == TR_REFACTOR ? c->an.n : c->tk.ntasks;
+    const long long items = phase == TR_REFACTOR ? c->an.n : phase == TR_DENSE ? c->dense_grid : c->tk.ntasks;
     const long long m = std::min(items, max_items);
     CK(cudaDeviceSynchronize());
     if (phase == TR_REFACTOR) {

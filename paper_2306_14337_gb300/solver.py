@@ -50,7 +50,7 @@ class KKTSolver:
                  pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
                  solve_ctas=0, update_map_budget=0, trace=False, max_batch=1, unpublished_row=-1,
                  poll_ns_max=0, refactor_big_warps=0, symmetric=False, jacobi_sweeps=8, values=None,
-                 row_perm=None, dense_block=0, device=0):
+                 row_perm=None, dense_block=0, refactor_row_cap=0, device=0):
         self._lib = _capi.load()
         self.n = int(n)
         self._rp = _i32(indptr)
@@ -82,6 +82,7 @@ class KKTSolver:
         opt.symmetric = int(bool(symmetric))
         opt.jacobi_sweeps = int(jacobi_sweeps)
         opt.dense_block = int(dense_block)
+        opt.refactor_row_cap = int(refactor_row_cap)
         self._row_perm = None
         if row_perm is not None:
             self._row_perm = _i32(row_perm)
@@ -235,8 +236,10 @@ class KKTSolver:
     def export_trace(self, phase: int) -> np.ndarray:
         """(items, 2) array of device claim / completion times in ns of the
         most recent launch of a phase (0 refactor, 1 forward, 2 backward,
-        3 transposed forward, 4 transposed backward)."""
-        m = max(self.n, self.stats()["n_tasks"])
+        3 transposed forward, 4 transposed backward, 5 dense-block tile tasks)."""
+        st = self.stats()
+        nt = (st["dense_rows"] + 31) // 32
+        m = max(self.n, st["n_tasks"], nt * (nt + 1) * (2 * nt + 1) // 6)
         buf = np.zeros(2 * m, dtype=np.uint64)
         k = C.c_longlong(0)
         check(self._lib.kkt_export_trace(self._h, int(phase), buf.ctypes.data_as(C.POINTER(C.c_ulonglong)),

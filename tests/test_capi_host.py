@@ -242,7 +242,8 @@ def test_dense_root_block_pattern(case, req):
         n = 200
         rp, ci = random_sparse_pattern(n, 0.01, 4, drop_diag=0.1)
     perm = oracle.min_degree(n, rp, ci)
-    S = KKTSolver(n, rp, ci, perm=perm, dense_block=req, device=None)
+    # the automatic choice is made for FP32 factors only
+    S = KKTSolver(n, rp, ci, perm=perm, dense_block=req, fp32=True, device=None)
     st = S.stats()
     vals = np.random.default_rng(0).standard_normal(len(ci))
     o = oracle.Oracle(n, rp, ci, vals, perm, equil=False)
@@ -267,15 +268,18 @@ def test_dense_root_block_pattern(case, req):
     assert np.all(np.diff(sym["level"][V]) >= 1)
     assert st["nnz_lu"] == len(sym["lu_ci"])
     # the checkpoint keeps the block
-    B = KKTSolver.from_analysis(S.save_analysis(), rp, ci, device=None)
+    B = KKTSolver.from_analysis(S.save_analysis(), rp, ci, fp32=True, device=None)
     assert B.stats()["dense_rows"] == st["dense_rows"]
     assert np.array_equal(B.export_dense_rows(), V)
 
 
 def test_dense_root_block_off_and_bad_option():
     s = config_sequence(1)
-    S = KKTSolver(s.n, s.indptr, s.indices, dense_block=-1, device=None)
+    S = KKTSolver(s.n, s.indptr, s.indices, dense_block=-1, fp32=True, device=None)
     assert S.stats()["dense_rows"] == 0 and S.export_dense_rows().size == 0
+    # FP64 factors take no automatic block (not faster on this GPU), only a requested one
+    assert KKTSolver(s.n, s.indptr, s.indices, device=None).stats()["dense_rows"] == 0
+    assert KKTSolver(s.n, s.indptr, s.indices, dense_block=150, device=None).stats()["dense_rows"] == 150
     with pytest.raises(KKTError) as ei:
         KKTSolver(s.n, s.indptr, s.indices, dense_block=-2, device=None)
     assert ei.value.status == _capi.KKT_ERR_ARG

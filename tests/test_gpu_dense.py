@@ -43,9 +43,9 @@ def _check(S, o, fp32):
     assert bad.size == 0, f"{bad.size} entries off; worst {np.max(d[bad] / tol[bad]):.3g} x tol"
 
 
-def _refined_omega(S, n, rp, ci, v, b):
+def _refined_omega(S, n, rp, ci, v, b, max_it=20):
     x = S.solve(_t(b))
-    info = S.refine(_t(b), x, 1e-14, 20)
+    info = S.refine(_t(b), x, 1e-14, max_it)
     assert info["converged"], info
     w = oracle.omega(n, rp, ci, v, b, x.cpu().numpy())
     assert w <= 1e-14, w
@@ -72,19 +72,23 @@ def test_dense_block_200bus(rows, fp32):
 
 @pytest.mark.parametrize("budget", [0, 1])
 @pytest.mark.parametrize("step", [0, 29])
-def test_dense_block_2000bus_default(budget, step):
-    """The automatic block of the 2,000-bus KKT, with the update maps and
-    without them (the binary-search path of the sparse rows)."""
+@pytest.mark.parametrize("fp32", [False, True])
+def test_dense_block_2000bus(budget, step, fp32):
+    """The 2,000-bus KKT with the automatic block (FP32 factors) or a
+    requested one of 200 rows (FP64), with the update maps and without them
+    (the binary-search path of the sparse rows)."""
     s = config_sequence(1)
     p = _perm("cfg1", s.n, s.indptr, s.indices)
     v, b = s.values(step), s.rhs(step)
-    S = KKTSolver(s.n, s.indptr, s.indices, perm=p, update_map_budget=budget)
-    assert S.stats()["dense_rows"] >= 96
+    S = KKTSolver(s.n, s.indptr, s.indices, perm=p, update_map_budget=budget, fp32=fp32,
+                  dense_block=0 if fp32 else 200, refine_mode="auto")
+    assert S.stats()["dense_rows"] >= 96 if fp32 else S.stats()["dense_rows"] == 200
     S.refactor(_t(v))
-    o = oracle.Oracle(s.n, s.indptr, s.indices, v, p)
+    o = oracle.Oracle(s.n, s.indptr, s.indices, v, p, tau_rel=2.0 ** -24 if fp32 else 1e-14)
     assert S.status()[1] == o.F.n_perturbed
-    _check(S, o, False)
-    _refined_omega(S, s.n, s.indptr, s.indices, v, b)
+    _check(S, o, fp32)
+    # FP32 factors of these systems (D over 16 decades) need many more solves
+    _refined_omega(S, s.n, s.indptr, s.indices, v, b, 60 if fp32 else 20)
 
 
 @pytest.mark.parametrize("n,density,seed,rows", [(60, 0.08, 7, 60), (200, 0.01, 4, 200), (200, 0.01, 4, 77)])
@@ -126,10 +130,10 @@ def test_dense_block_perturbed_pivot_closed_form():
     np.testing.assert_allclose(S.export_factors().cpu().numpy(), want, rtol=1e-13)
 
 
-@pytest.mark.parametrize("cfg,step,rows", [(0, 9, 100), (1, 29, 0)])
+@pytest.mark.parametrize("cfg,step,rows", [(0, 9, 100), (1, 29, 230)])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_dense_block_symmetric_ldlt(cfg, step, rows, fp32):
-    """LDL^T rows reduce only their upper part; k_dense_lu mirrors the block
+    """LDL^T rows reduce only their upper part and write it to both triangles of the block;
     and counts the inertia of its pivots with the sparse rows'."""
     s = config_sequence(cfg)
     p = _perm(f"cfg{cfg}", s.n, s.indptr, s.indices)
