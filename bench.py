@@ -4,6 +4,9 @@
 Workload (default): the 70,000-bus late-IPM system with FP32 factors and FP64
 refinement (KKT dimension 490,000, 4,914,000 stored entries, 4 value sets with
 D_x, D_s log-uniform in [1e-8, 1e8]), the largest single-GPU configuration.
+The values are symmetric (Eq. 4), so the FP32 factors are computed in the
+LDL^T form (same storage and solves as LU, half the refactorization's
+arithmetic), with the dense root block factored by k_dense_lu.
 ``--workload 2000bus_fp64_adjoint`` runs the 2,000-bus plain FP64 sequence
 (n = 14,000, 30 value sets).  One step is one KKT system through the whole
 path: refactorization, solve, iterative refinement to scaled residual 1e-14,
@@ -43,7 +46,11 @@ import numpy as np
 METRIC = "refactor+solve µs per KKT system and HBM GB/s on 1 GB300; batched/FP32 vs plain"
 UNIT = "us/system"
 WORKLOADS = {
-    "70000bus_fp32_refined": dict(cfg=3, fp32=True, refine="auto"),
+    # the KKT values are symmetric (Eq. 4): the FP32 factors are the LDL^T form
+    # (the same L and U storage; half the refactorization's arithmetic)
+    "70000bus_fp32_refined": dict(cfg=3, fp32=True, refine="auto", symmetric=True),
+    # the same form on the 10,000-bus grid (a smaller case of the same kernels)
+    "10000bus_fp32_refined": dict(cfg=2, fp32=True, refine="auto", symmetric=True),
     "2000bus_fp64_adjoint": dict(cfg=1, fp32=False, refine="classic"),
     "200bus_fp64": dict(cfg=0, fp32=False, refine="classic"),
     # 64 scenario systems of the 10,000-bus grid, batched; sharded across
@@ -161,7 +168,7 @@ def load_peaks():
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("kkt.cu", "kernels.cuh"):
+    for f in ("kkt.cu", "kernels.cuh", "dense.cu"):
         with open(os.path.join(ROOT, "paper_2306_14337_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -506,7 +513,8 @@ def run_native(args, ws, rank, local):
     wl = WORKLOADS[args.workload]
     seq = config_sequence(wl["cfg"])
     n, nnz, K = seq.n, seq.nnz, seq.steps
-    S = KKTSolver(n, seq.indptr, seq.indices, fp32=wl["fp32"], refine_mode=wl["refine"], device=local)
+    S = KKTSolver(n, seq.indptr, seq.indices, fp32=wl["fp32"], refine_mode=wl["refine"],
+                  symmetric=wl.get("symmetric", False), device=local)
     dname = "f32" if wl["fp32"] else "f64"
     rng = np.random.default_rng(1234 + rank)
     vals = [torch.tensor(seq.values(k), device=dev) for k in range(K)]
@@ -670,7 +678,8 @@ def run_native(args, ws, rank, local):
         "dtype": dname, "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "nnz": nnz, "nnz_lu": st["nnz_lu"],
                    "levels": st["n_levels"], "value_sets": K, "dense_rows": st["dense_rows"],
-                   "factors": "FP32, FP64 residual/refinement/pivot test" if wl["fp32"] else "FP64",
+                   "factors": ("FP32, FP64 residual/refinement/pivot test" if wl["fp32"] else "FP64")
+                              + (", LDL^T of the symmetric values" if wl.get("symmetric") else ", LU"),
                    "refine": wl["refine"],
                    "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                    "parallelism": f"replicas x{ws}"},
