@@ -107,57 +107,93 @@ __device__ __forceinline__ double abs_nan_inf(double v) { return isnan(v) ? INFI
 
 // s_i = 2^-floor(floor(log2 r_i) / 2), r_i = max_j |a_ij| (1 for a zero or
 // non-finite row); sp[new] = s[old]; ||A||_inf; non-finite input flagged.
-__global__ void k_scale(DevPattern P, const double *__restrict__ aval, double *__restrict__ s_orig,
-                        double *__restrict__ sp, unsigned long long *norms, int *status, int equil) {
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const int sub = threadIdx.x & 7;
-    double rmax = 0.0, rsum = 0.0;
-    bool bad = false;
-    const int r = g;
-    if (r < P.n) {
-        for (int p = P.a_rp[r] + sub; p < P.a_rp[r + 1]; p += 8) {
-            double a = fabs(aval[p]);
-            if (!isfinite(a)) bad = true;
-            rmax = fmax(rmax, a);
-            rsum += a;
-        }
-    }
-    for (int o = 4; o > 0; o >>= 1) {
-        rmax = fmax(rmax, __shfl_xor_sync(FULL, rmax, o));
-        rsum += __shfl_xor_sync(FULL, rsum, o);
-        bad |= __shfl_xor_sync(FULL, (int)bad, o);
-    }
-    if (r < P.n && sub == 0) {
-        double s = 1.0;
-        if (equil && !bad && rmax > 0.0) s = ldexp(1.0, -floor_half(ilogb(rmax)));
-        s_orig[r] = s;
-        sp[P.iperm[r]] = s;
-        if (bad) atomicExch(status + ST_NONFINITE, 1);
-        else atomic_max_nonneg(norms + NM_ANORM, rsum);
-    }
+// Norms over the rows reduce inside the CTA first (warp shuffles, then shared
+// memory) and enter the device word with one atomic per CTA: the rows of a
+// 490,000-row matrix must not serialize on one address.  The kernels walk the
+// rows grid-stride, a warp taking 4 rows at a time (8 lanes per row).
+constexpr int RTHREADS = 256;
+
+// max over the CTA of non-negative v (thread 0's return value is valid)
+__device__ __forceinline__ double cta_max(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();                                   // red may still be read by a previous call
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 1; k < (int)(blockDim.x >> 5); k++) v = fmax(v, red[k]);
+    return v;
 }
 
-// max |A'| (for the pivot threshold) and ||A||_1 (for transposed residuals)
-__global__ void k_amax(DevPattern P, const double *__restrict__ aval, const double *__restrict__ s_orig,
-                       unsigned long long *norms) {
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+__global__ void __launch_bounds__(RTHREADS)
+k_scale(DevPattern P, const double *__restrict__ aval, double *__restrict__ s_orig,
+        double *__restrict__ sp, unsigned long long *norms, int *status, int equil) {
+    __shared__ double red[RTHREADS / 32];
     const int sub = threadIdx.x & 7;
-    double m = 0.0, csum = 0.0;
-    if (r < P.n) {
-        const double sr = s_orig[r];
-        for (int p = P.a_rp[r] + sub; p < P.a_rp[r + 1]; p += 8) {
-            double a = fabs(aval[p]) * sr * s_orig[P.a_ci[p]];
-            m = fmax(m, a);
+    const long long step = (long long)gridDim.x * (blockDim.x >> 3);
+    double nmax = 0.0;                                 // ||A||_inf over the finite rows seen
+    for (long long r0 = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; r0 < P.n; r0 += step) {
+        const int r = (int)r0 + ((threadIdx.x & 31) >> 3);
+        double rmax = 0.0, rsum = 0.0;
+        bool bad = false;
+        if (r < P.n) {
+            for (int p = P.a_rp[r] + sub; p < P.a_rp[r + 1]; p += 8) {
+                double a = fabs(aval[p]);
+                if (!isfinite(a)) bad = true;
+                rmax = fmax(rmax, a);
+                rsum += a;
+            }
         }
-        for (int q = P.at_rp[r] + sub; q < P.at_rp[r + 1]; q += 8) csum += fabs(aval[P.at_src[q]]);
+        for (int o = 4; o > 0; o >>= 1) {
+            rmax = fmax(rmax, __shfl_xor_sync(FULL, rmax, o));
+            rsum += __shfl_xor_sync(FULL, rsum, o);
+            bad |= __shfl_xor_sync(FULL, (int)bad, o);
+        }
+        if (r < P.n && sub == 0) {
+            double s = 1.0;
+            if (equil && !bad && rmax > 0.0) s = ldexp(1.0, -floor_half(ilogb(rmax)));
+            s_orig[r] = s;
+            sp[P.iperm[r]] = s;
+            if (bad) atomicExch(status + ST_NONFINITE, 1);
+            else nmax = fmax(nmax, rsum);
+        }
     }
-    for (int o = 4; o > 0; o >>= 1) {
-        m = fmax(m, __shfl_xor_sync(FULL, m, o));
-        csum += __shfl_xor_sync(FULL, csum, o);
+    nmax = cta_max(nmax, red);
+    if (threadIdx.x == 0) atomic_max_nonneg(norms + NM_ANORM, nmax);
+}
+
+__global__ void __launch_bounds__(RTHREADS)
+k_amax(DevPattern P, const double *__restrict__ aval, const double *__restrict__ s_orig,
+       unsigned long long *norms) {
+    __shared__ double red[RTHREADS / 32];
+    const int sub = threadIdx.x & 7;
+    const long long step = (long long)gridDim.x * (blockDim.x >> 3);
+    double mmax = 0.0, cmax = 0.0;                     // max|A'|, ||A||_1 over the finite rows seen
+    for (long long r0 = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; r0 < P.n; r0 += step) {
+        const int r = (int)r0 + ((threadIdx.x & 31) >> 3);
+        double m = 0.0, csum = 0.0;
+        if (r < P.n) {
+            const double sr = s_orig[r];
+            for (int p = P.a_rp[r] + sub; p < P.a_rp[r + 1]; p += 8) {
+                double a = fabs(aval[p]) * sr * s_orig[P.a_ci[p]];
+                m = fmax(m, a);
+            }
+            for (int q = P.at_rp[r] + sub; q < P.at_rp[r + 1]; q += 8) csum += fabs(aval[P.at_src[q]]);
+        }
+        for (int o = 4; o > 0; o >>= 1) {
+            m = fmax(m, __shfl_xor_sync(FULL, m, o));
+            csum += __shfl_xor_sync(FULL, csum, o);
+        }
+        if (r < P.n && sub == 0) {
+            if (isfinite(m)) mmax = fmax(mmax, m);
+            if (isfinite(csum)) cmax = fmax(cmax, csum);
+        }
     }
-    if (r < P.n && sub == 0) {
-        if (isfinite(m)) atomic_max_nonneg(norms + NM_AMAX, m);
-        if (isfinite(csum)) atomic_max_nonneg(norms + NM_A1NORM, csum);
+    mmax = cta_max(mmax, red);
+    cmax = cta_max(cmax, red);
+    if (threadIdx.x == 0) {
+        atomic_max_nonneg(norms + NM_AMAX, mmax);
+        atomic_max_nonneg(norms + NM_A1NORM, cmax);
     }
 }
 
@@ -1864,41 +1900,44 @@ k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T
 // ---------------------------------------------------------------------------
 // FP64 residual rho = b - A x (or b - A^T x), 8 lanes per row, fused with
 // ||rho||_inf, ||x||_inf, ||b||_inf.
-__global__ void k_resid(DevPattern P, const double *__restrict__ aval, const double *__restrict__ b,
-                        const double *__restrict__ x, double *__restrict__ rho,
-                        unsigned long long *norms, int transpose) {
-    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+__global__ void __launch_bounds__(RTHREADS)
+k_resid(DevPattern P, const double *__restrict__ aval, const double *__restrict__ b,
+        const double *__restrict__ x, double *__restrict__ rho,
+        unsigned long long *norms, int transpose) {
+    __shared__ double red[RTHREADS / 32];
     const int sub = threadIdx.x & 7;
-    double acc = 0.0;
-    if (r < P.n) {
-        if (!transpose) {
-            for (int p = P.a_rp[r] + sub; p < P.a_rp[r + 1]; p += 8) acc += aval[p] * x[P.a_ci[p]];
-        } else {
-            for (int q = P.at_rp[r] + sub; q < P.at_rp[r + 1]; q += 8) {
-                const int k = P.at_src[q];
-                acc += aval[k] * x[P.a_row[k]];
+    const long long step = (long long)gridDim.x * (blockDim.x >> 3);
+    double rmax = 0.0, xmax = 0.0, bmax = 0.0;
+    for (long long r0 = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; r0 < P.n; r0 += step) {
+        const int r = (int)r0 + ((threadIdx.x & 31) >> 3);
+        double acc = 0.0;
+        if (r < P.n) {
+            if (!transpose) {
+                for (int p = P.a_rp[r] + sub; p < P.a_rp[r + 1]; p += 8) acc += aval[p] * x[P.a_ci[p]];
+            } else {
+                for (int q = P.at_rp[r] + sub; q < P.at_rp[r + 1]; q += 8) {
+                    const int k = P.at_src[q];
+                    acc += aval[k] * x[P.a_row[k]];
+                }
             }
         }
+        for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (r < P.n && sub == 0) {
+            const double br = b[r];
+            const double rv = br - acc;
+            rho[r] = rv;
+            rmax = fmax(rmax, abs_nan_inf(rv));
+            xmax = fmax(xmax, abs_nan_inf(x[r]));
+            bmax = fmax(bmax, abs_nan_inf(br));
+        }
     }
-    for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-    double rv = 0.0, xv = 0.0, bv = 0.0;
-    if (r < P.n && sub == 0) {
-        const double br = b[r];
-        rv = br - acc;
-        rho[r] = rv;
-        rv = abs_nan_inf(rv);
-        xv = abs_nan_inf(x[r]);
-        bv = abs_nan_inf(br);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        rv = fmax(rv, __shfl_xor_sync(FULL, rv, o));
-        xv = fmax(xv, __shfl_xor_sync(FULL, xv, o));
-        bv = fmax(bv, __shfl_xor_sync(FULL, bv, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(norms + NM_RMAX, rv);
-        atomic_max_nonneg(norms + NM_XMAX, xv);
-        atomic_max_nonneg(norms + NM_BMAX, bv);
+    rmax = cta_max(rmax, red);
+    xmax = cta_max(xmax, red);
+    bmax = cta_max(bmax, red);
+    if (threadIdx.x == 0) {
+        atomic_max_nonneg(norms + NM_RMAX, rmax);
+        atomic_max_nonneg(norms + NM_XMAX, xmax);
+        atomic_max_nonneg(norms + NM_BMAX, bmax);
     }
 }
 
@@ -2400,6 +2439,9 @@ struct DeviceGuard {
 };
 
 inline int blocks_for(long long threads, int bs) { return (int)((threads + bs - 1) / bs); }
+// CTAs of the row-norm kernels (k_scale, k_amax, k_resid): 8 lanes per row,
+// grid-stride beyond 2,048 CTAs, so the per-CTA atomics stay few
+inline int norm_blocks(long long n) { return std::max(1, std::min(blocks_for(8 * n, RTHREADS), 2048)); }
 
 // Raise a kernel's dynamic shared-memory limit on the current device to at
 // least `bytes`.  The limit belongs to the kernel, not to a context, so it is
@@ -3327,11 +3369,11 @@ kkt_status kkt_refactor(kkt_ctx *c, const double *values_dev, kkt_stream stream)
     const int n = c->an.n;
     CK(cudaMemsetAsync(c->d_norms, 0, NM_WORDS * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(c->d_status + ST_NEGATIVE, 0, 2 * sizeof(int), s));   // this refactorization's inertia
-    k_scale<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, values_dev, c->d_s, c->d_sp, c->d_norms,
+    k_scale<<<norm_blocks(n), RTHREADS, 0, s>>>(c->P, values_dev, c->d_s, c->d_sp, c->d_norms,
                                                      c->d_status, c->opt.equilibrate);
     CK(cudaGetLastError());
     c->launches++;
-    k_amax<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, values_dev, c->d_s, c->d_norms);
+    k_amax<<<norm_blocks(n), RTHREADS, 0, s>>>(c->P, values_dev, c->d_s, c->d_norms);
     CK(cudaGetLastError());
     c->launches++;
     kkt_status r = c->opt.factor_fp32 ? launch_refactor<float>(c, s) : launch_refactor<double>(c, s);
@@ -3474,7 +3516,7 @@ static kkt_status residual_omega(kkt_ctx *c, const double *b, const double *x, i
                                  cudaStream_t s, double *omega) {
     const int n = c->an.n;
     CK(cudaMemsetAsync(c->d_norms + NM_RMAX, 0, 3 * sizeof(unsigned long long), s));
-    k_resid<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, c->values, b, x, c->d_rho, c->d_norms, transpose);
+    k_resid<<<norm_blocks(n), RTHREADS, 0, s>>>(c->P, c->values, b, x, c->d_rho, c->d_norms, transpose);
     CK(cudaGetLastError());
     c->launches++;
     CK(cudaMemcpyAsync(c->h_norms, c->d_norms, NM_WORDS * sizeof(unsigned long long),
@@ -4127,10 +4169,10 @@ static kkt_status q_record(kkt_queue *q, int n_refine, double *omega_dev, cudaSt
         const QSys &h = q->h_sys[k];
         const int n = c->an.n;
         CK(cudaMemsetAsync(c->d_norms, 0, NM_WORDS * sizeof(unsigned long long), s));
-        k_scale<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, h.values, c->d_s, c->d_sp, c->d_norms, q->d_status,
+        k_scale<<<norm_blocks(n), RTHREADS, 0, s>>>(c->P, h.values, c->d_s, c->d_sp, c->d_norms, q->d_status,
                                                          c->opt.equilibrate);
         CK(cudaGetLastError());
-        k_amax<<<blocks_for(8LL * n, 256), 256, 0, s>>>(c->P, h.values, c->d_s, c->d_norms);
+        k_amax<<<norm_blocks(n), RTHREADS, 0, s>>>(c->P, h.values, c->d_s, c->d_norms);
         CK(cudaGetLastError());
         CK(cudaMemsetAsync(c->d_lu, 0xff, (size_t)c->nnz_lu * sizeof(T), s));
         CK(cudaMemsetAsync(c->d_rcp, 0xff, (size_t)n * sizeof(T), s));
@@ -4160,7 +4202,7 @@ static kkt_status q_record(kkt_queue *q, int n_refine, double *omega_dev, cudaSt
                 kkt_ctx *c = q->ctx[k];
                 const QSys &h = q->h_sys[k];
                 CK(cudaMemsetAsync(c->d_norms + NM_RMAX, 0, 3 * sizeof(unsigned long long), s));
-                k_resid<<<blocks_for(8LL * c->an.n, 256), 256, 0, s>>>(c->P, h.values, h.b, h.x, c->d_rho,
+                k_resid<<<norm_blocks(c->an.n), RTHREADS, 0, s>>>(c->P, h.values, h.b, h.x, c->d_rho,
                                                                       c->d_norms, 0);
                 CK(cudaGetLastError());
                 q->launches++;
@@ -4181,7 +4223,7 @@ static kkt_status q_record(kkt_queue *q, int n_refine, double *omega_dev, cudaSt
             kkt_ctx *c = q->ctx[k];
             const QSys &h = q->h_sys[k];
             CK(cudaMemsetAsync(c->d_norms + NM_RMAX, 0, 3 * sizeof(unsigned long long), s));
-            k_resid<<<blocks_for(8LL * c->an.n, 256), 256, 0, s>>>(c->P, h.values, h.b, h.x, c->d_rho, c->d_norms, 0);
+            k_resid<<<norm_blocks(c->an.n), RTHREADS, 0, s>>>(c->P, h.values, h.b, h.x, c->d_rho, c->d_norms, 0);
             CK(cudaGetLastError());
             k_omega<<<1, 1, 0, s>>>(c->d_norms, omega_dev + k);
             CK(cudaGetLastError());
