@@ -167,3 +167,66 @@ def test_dense_block_matches_sparse_rows():
     f1 = B.export_factors()
     B.refactor(_t(v))
     assert torch.equal(B.export_factors(), f1)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_dense_block_rows_in_batched_and_queued_refactorizations(fp32):
+    """The batched and queued refactorizations take the dense root block's
+    rows as sparse rows (its own pivot steps have no update map: their
+    targets are found by binary search); their factors must still match the
+    oracle, and the single-system path of the same context (k_dense_lu) too."""
+    from paper_2306_14337_gb300 import KKTQueue
+    s = config_sequence(0, asym=0.05)
+    p = _perm("cfg0", s.n, s.indptr, s.indices)
+    tau = 2.0 ** -24 if fp32 else 1e-14
+    B = 6
+    vals = np.stack([s.values(4, sc) for sc in range(1, B + 1)], axis=1)
+    S = KKTSolver(s.n, s.indptr, s.indices, perm=p, fp32=fp32, dense_block=100, max_batch=B)
+    assert S.stats()["dense_rows"] == 100
+    S.batch_refactor(torch.tensor(vals, device=DEV))
+    for sc in (0, 3, 5):
+        o = oracle.Oracle(s.n, s.indptr, s.indices, vals[:, sc], p, tau_rel=tau)
+        rp, ci, ref, E = o.F.lu_csr()
+        got = on_fill(S, rp, ci, S.batch_export_factors(sc).cpu().numpy())
+        tol = np.maximum(1e-5 * np.abs(ref), 4 * E * 2.0 ** 29) if fp32 else np.maximum(1e-11 * np.abs(ref), 4 * E)
+        assert np.all(np.abs(got - ref) <= tol)
+    # a queue of two contexts with dense blocks
+    sols = [KKTSolver(s.n, s.indptr, s.indices, perm=p, fp32=fp32, dense_block=100) for _ in range(2)]
+    Q = KKTQueue(sols)
+    qv = [torch.tensor(vals[:, j], device=DEV) for j in range(2)]
+    qb = [torch.tensor(s.csr(4, j + 1) @ s.x_true(4, j + 1), device=DEV) for j in range(2)]
+    qx = [torch.zeros_like(b) for b in qb]
+    Q.run(qv, qb, qx, n_refine=1)
+    torch.cuda.synchronize()
+    for j in range(2):
+        o = oracle.Oracle(s.n, s.indptr, s.indices, vals[:, j], p, tau_rel=tau)
+        rp, ci, ref, E = o.F.lu_csr()
+        got = on_fill(sols[j], rp, ci, sols[j].export_factors().cpu().numpy())
+        tol = np.maximum(1e-5 * np.abs(ref), 4 * E * 2.0 ** 29) if fp32 else np.maximum(1e-11 * np.abs(ref), 4 * E)
+        assert np.all(np.abs(got - ref) <= tol)
+    # the single-system refactorization of one of the queue's contexts
+    sols[0].refactor(qv[0])
+    o = oracle.Oracle(s.n, s.indptr, s.indices, vals[:, 0], p, tau_rel=tau)
+    _check(sols[0], o, fp32)
+
+
+def test_dense_block_with_value_aware_row_permutation():
+    """A value-aware context (row permutation from the matching) with a dense
+    root block: factors of Q A against the oracle with the same Q and ordering."""
+    from kktgen import kkt_sequence
+    s = kkt_sequence(200, 260, 40, seed=77, steps=3, reg=0.0, asym=0.05)
+    v = s.values(1)
+    q = oracle.max_product_matching(s.n, s.indptr, s.indices, v)
+    qrp, qci, qv = oracle.row_permuted(s.n, s.indptr, s.indices, v, q)
+    p = oracle.min_degree(s.n, qrp, qci)
+    S = KKTSolver(s.n, s.indptr, s.indices, row_perm=q, perm=p, dense_block=64)
+    assert 0 < S.stats()["dense_rows"] <= 64
+    S.refactor(_t(v))
+    o = oracle.Oracle(s.n, qrp, qci, qv, p)
+    assert S.status()[1] == o.F.n_perturbed
+    _check(S, o, False)
+    b = s.rhs(1)
+    x = S.solve(_t(b))
+    info = S.refine(_t(b), x, 1e-14, 20)
+    assert info["converged"], info
+    assert oracle.omega(s.n, s.indptr, s.indices, v, b, x.cpu().numpy()) <= 1e-14
