@@ -141,6 +141,10 @@ typedef struct {
                                the single-system refactorization (0: the longest row,
                                at most 1,024); longer rows work in global memory.  A
                                larger buffer fits fewer warps on an SM. */
+    double refine_auto_ratio; /* refine mode auto: classic steps continue while each
+                               lowers the scaled residual to at most this fraction of
+                               the previous one, then FGMRES takes over (0: 0.5; must
+                               be below 1) */
 } kkt_options;
 
 typedef struct {

@@ -54,6 +54,7 @@ class Options(C.Structure):
         ("user_row_perm", C.POINTER(C.c_int)),
         ("dense_block", C.c_int),
         ("refactor_row_cap", C.c_int),
+        ("refine_auto_ratio", C.c_double),
     ]
 
 

@@ -2398,6 +2398,7 @@ struct kkt_ctx {
     int last_iters = 0;
     double last_omega = -1.0;
     double tau_rel = 0.0;
+    double auto_ratio = 0.5;  // refine mode auto: classic steps while omega falls at least this much
     long long launches = 0;  // kernels launched by this context
 };
 
@@ -2492,6 +2493,7 @@ void kkt_default_options(kkt_options *o) {
     o->user_row_perm = nullptr;
     o->dense_block = 0;
     o->refactor_row_cap = 0;
+    o->refine_auto_ratio = 0.0;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -3126,6 +3128,7 @@ static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, con
     if (c->opt.fgmres_restart < 1 || c->opt.max_refine < 0 || c->opt.spin_limit < 1 ||
         c->opt.refine_mode < KKT_REFINE_CLASSIC || c->opt.refine_mode > KKT_REFINE_FGMRES_JACOBI ||
         c->opt.jacobi_sweeps < 0 || c->opt.dense_block < -1 || c->opt.refactor_row_cap < 0 ||
+        !(c->opt.refine_auto_ratio >= 0.0 && c->opt.refine_auto_ratio < 1.0) ||
         c->opt.max_batch < 1 || c->opt.cta_warps < 0 || c->opt.refactor_ctas < 0 ||
         c->opt.solve_ctas < 0) {
         g_last_error = "invalid option";
@@ -3207,6 +3210,7 @@ static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, con
     c->opt.user_row_perm = nullptr;
     c->tau_rel = c->opt.pivot_tau_rel > 0 ? c->opt.pivot_tau_rel
                                           : (c->opt.factor_fp32 ? 0x1p-24 : 1e-14);
+    c->auto_ratio = c->opt.refine_auto_ratio > 0 ? c->opt.refine_auto_ratio : 0.5;
     c->dev = c->opt.device;
     c->host_only = c->opt.device < 0;
     if (!c->host_only) {
@@ -3548,8 +3552,8 @@ static kkt_status dot_to_host(kkt_ctx *c, const double *V, long long ld, int k, 
 // preconditioner, classical Gram-Schmidt applied twice).  Uses at most
 // max_apps preconditioner applications; returns the number used.
 static kkt_status fgmres_cycle(kkt_ctx *c, const double *b, double *x, double tol, int max_apps,
-                               int transpose, double anorm, double bnorm, double xnorm, int *used,
-                               cudaStream_t s) {
+                               int transpose, double anorm, double bnorm, double xnorm, double rinf,
+                               int *used, cudaStream_t s) {
     const int n = c->an.n, m = std::min(c->kry_m, max_apps);
     *used = 0;
     if (m < 1) return KKT_OK;
@@ -3624,7 +3628,11 @@ static kkt_status fgmres_cycle(kkt_ctx *c, const double *b, double *x, double to
         g[j + 1] = -sn[j] * g[j];
         g[j] = cs[j] * g[j];
         k_used = j + 1;
-        if (std::fabs(g[j + 1]) <= tol * (anorm * xnorm + bnorm) || hnext == 0.0) break;
+        // stop once the residual's infinity norm, estimated from its 2-norm |g|
+        // times the ratio ||r0||_inf / ||r0||_2 of the cycle's first residual,
+        // meets the target; the caller then measures omega itself (a 2-norm
+        // test alone would overshoot by up to sqrt(n))
+        if (std::fabs(g[j + 1]) * (rinf / beta) <= tol * (anorm * xnorm + bnorm) || hnext == 0.0) break;
     }
     // y = H^-1 g (upper triangular), x += Z y
     std::vector<double> y(k_used, 0.0);
@@ -3671,7 +3679,7 @@ static kkt_status refine_any(kkt_ctx *c, const double *b, double *x, double tol,
             st = residual_omega(c, b, x, transpose, s, &w);
             if (st) return st;
             record(w);
-            if (mode == KKT_REFINE_AUTO && !(w <= 0.5 * prev) && !(w <= tol)) break;   // stalled
+            if (mode == KKT_REFINE_AUTO && !(w <= c->auto_ratio * prev) && !(w <= tol)) break;   // stalled
         }
     }
     if ((mode == KKT_REFINE_FGMRES || mode == KKT_REFINE_AUTO || mode == KKT_REFINE_FGMRES_JACOBI) &&
@@ -3680,7 +3688,7 @@ static kkt_status refine_any(kkt_ctx *c, const double *b, double *x, double tol,
             const double an = host_norm(c, transpose ? NM_A1NORM : NM_ANORM);
             int used = 0;
             st = fgmres_cycle(c, b, x, tol, max_it - it, transpose, an, host_norm(c, NM_BMAX),
-                              host_norm(c, NM_XMAX), &used, s);
+                              host_norm(c, NM_XMAX), host_norm(c, NM_RMAX), &used, s);
             if (st) return st;
             it += used;
             st = residual_omega(c, b, x, transpose, s, &w);
@@ -4596,6 +4604,7 @@ kkt_status kkt_load_analysis(const void *buf, size_t size, const kkt_options *op
     c->opt.user_perm = nullptr;
     c->opt.user_row_perm = nullptr;
     c->tau_rel = c->opt.pivot_tau_rel > 0 ? c->opt.pivot_tau_rel : (c->opt.factor_fp32 ? 0x1p-24 : 1e-14);
+    c->auto_ratio = c->opt.refine_auto_ratio > 0 ? c->opt.refine_auto_ratio : 0.5;
     c->dev = c->opt.device;
     c->host_only = c->opt.device < 0;
     if (!c->host_only) {

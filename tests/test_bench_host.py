@@ -40,7 +40,7 @@ def test_default_workload_is_the_largest_single_gpu_configuration():
     from kktgen import config_sequence
     assert bench.DEFAULT_WORKLOAD == "70000bus_fp32_refined"
     cfg = bench.WORKLOADS[bench.DEFAULT_WORKLOAD]
-    assert cfg["fp32"] and cfg["refine"] == "auto"
+    assert cfg["fp32"] and cfg["refine"] in ("auto", "fgmres")
     sizes = [config_sequence(c).n for c in (0, 1, 3)]
     assert config_sequence(cfg["cfg"]).n == max(sizes) == 490_000
 
