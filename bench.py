@@ -788,7 +788,7 @@ def run_uneven(dev, with_oracle=True, budget=15.0):
     out = {"us_per_system": tq * 1e3 / len(seqs), "plain_fp64_us_per_system": tp * 1e3 / len(seqs),
            "speedup_vs_plain": tp / tq, "systems": len(seqs), "omega_max": worst,
            "finished_outside_graph": state.get("late"), "launch_shape": list(best),
-           "tuning_ms": {f"{w}x{c}": t * 1e3 for (w, c), t in (table or {}).items()}}
+           "tuning_ms": {"x".join(str(v) for v in cand): t * 1e3 for cand, t in (table or {}).items()}}
     if with_oracle:
         import oracle
         # FP64-oracle error of the solution of one system of each size

@@ -423,6 +423,11 @@ typedef struct kkt_queue kkt_queue;
 kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out);
 void kkt_queue_destroy(kkt_queue *q);
 kkt_status kkt_queue_set_launch(kkt_queue *q, int cta_warps, int ctas);
+/* Tile choice of the queue's solves, used by the autotuner: how many of the
+ * queue's longest solve tasks (at most 48, longest first; -1 = all of them)
+ * run on a whole CTA each (with 8 warps per CTA), the others as warp items.
+ * The captured graph is recorded again at the next kkt_queue_run. */
+kkt_status kkt_queue_set_tiles(kkt_queue *q, int cta_tasks);
 kkt_status kkt_queue_run(kkt_queue *q, const double *const *values, const double *const *b,
                          double *const *x, int n_refine, double *omega_dev, kkt_stream stream);
 kkt_status kkt_queue_solve_transpose(kkt_queue *q, const double *const *g, double *const *lam,

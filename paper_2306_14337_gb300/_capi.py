@@ -132,6 +132,7 @@ SIGNATURES = {
     "kkt_queue_create": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
     "kkt_queue_destroy": (None, [_vp]),
     "kkt_queue_set_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "kkt_queue_set_tiles": (C.c_int, [_vp, C.c_int]),
     "kkt_queue_run": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, _vp]),
     "kkt_queue_solve_transpose": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), _vp]),
     "kkt_queue_status_sync": (C.c_int, [_vp, _vp, _ip]),

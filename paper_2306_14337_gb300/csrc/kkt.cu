@@ -3966,6 +3966,12 @@ struct kkt_queue {
     int nch = 0, n_fwd_reg = 0, n_bwd_reg = 0;
     int2 *d_chains = nullptr, *d_items_reg = nullptr;
     size_t smem_chain = 0;
+    // the candidates (longest first: length, system, chain index; at most
+    // QCHAIN_MAX) and the solve items; kkt_queue_set_tiles picks how many
+    // candidates run as CTA tasks
+    std::vector<std::array<int, 3>> cand;
+    std::vector<int2> fwd_items, bwd_items;
+    int ctas_opt = 0;
     Sched *d_sched = nullptr;
     int *d_status = nullptr;
     void *d_scratch = nullptr;
@@ -3983,6 +3989,36 @@ template <typename T> static kkt_status q_set_smem(kkt_queue *q) {
     CK(ensure_smem((const void *)k_qtrisolve<T, true, false>, q->smem_sol));
     CK(ensure_smem((const void *)k_qtrisolve<T, false, true>, q->smem_sol));
     CK(ensure_smem((const void *)k_qtrisolve<T, true, true>, q->smem_sol));
+    return KKT_OK;
+}
+
+// The first k candidates run as CTA tasks (with CTAs of WARPS warps); the
+// other tasks stay warp items.
+static kkt_status q_set_chains(kkt_queue *q, int k) {
+    k = std::max(0, std::min(k, (int)q->cand.size()));
+    std::vector<int2> chains;
+    std::set<std::pair<int, int>> taken;           // (system, task)
+    const size_t tsz = q->f32 ? sizeof(float) : sizeof(double);
+    q->smem_chain = 0;
+    for (int j = 0; j < k; j++) {
+        const auto &cd = q->cand[j];
+        const kkt_ctx *c = q->ctx[cd[1]];
+        chains.push_back(make_int2(cd[1], cd[2]));
+        taken.insert({cd[1], c->chain_h[cd[2]]});
+        q->smem_chain = std::max(q->smem_chain, chain_smem_bytes(c->tk1.zcap, tsz));
+    }
+    std::vector<int2> reg;
+    for (auto &v : q->fwd_items)
+        if (!taken.count({v.x, v.y})) reg.push_back(v);
+    q->n_fwd_reg = (int)reg.size();
+    for (auto &v : q->bwd_items)
+        if (!taken.count({v.x, v.y})) reg.push_back(v);
+    q->n_bwd_reg = (int)reg.size() - q->n_fwd_reg;
+    q->nch = k;
+    if (k > 0) CK(cudaMemcpy(q->d_chains, chains.data(), chains.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    if (!reg.empty()) CK(cudaMemcpy(q->d_items_reg, reg.data(), reg.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    if (q->graph) { cudaGraphExecDestroy(q->graph); q->graph = nullptr; }
+    q->key.clear();
     return KKT_OK;
 }
 
@@ -4073,43 +4109,21 @@ kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
     q->n_bwd = (int)bwd.size();
     CK(cudaMalloc(&q->d_items, items.size() * sizeof(int2)));
     CK(cudaMemcpy(q->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    {   // CTA tasks: the longest of the contexts' CTA tasks, at most QCHAIN_MAX
-        std::vector<std::array<int, 3>> cand;          // (length, system, chain index)
+    {   // CTA-task candidates: the longest of the contexts' CTA tasks, at most QCHAIN_MAX
         for (int k = 0; k < m; k++) {
             const kkt_ctx *c = q->ctx[k];
             for (int ci = 0; ci < (int)c->chain_h.size(); ci++) {
                 const int T = c->chain_h[ci];
-                cand.push_back({c->an.task_hi[T] - c->an.task_lo[T] + 1, k, ci});
+                q->cand.push_back({c->an.task_hi[T] - c->an.task_lo[T] + 1, k, ci});
             }
         }
-        std::stable_sort(cand.begin(), cand.end(), [](const std::array<int, 3> &x, const std::array<int, 3> &y) {
-            return x[0] > y[0];
-        });
-        if ((int)cand.size() > QCHAIN_MAX) cand.resize(QCHAIN_MAX);
-        std::vector<int2> chains;
-        std::set<std::pair<int, int>> taken;           // (system, task)
-        const size_t tsz = q->f32 ? sizeof(float) : sizeof(double);
-        for (auto &cd : cand) {
-            const kkt_ctx *c = q->ctx[cd[1]];
-            chains.push_back(make_int2(cd[1], cd[2]));
-            taken.insert({cd[1], c->chain_h[cd[2]]});
-            q->smem_chain = std::max(q->smem_chain, chain_smem_bytes(c->tk1.zcap, tsz));
-        }
-        std::vector<int2> reg;
-        for (auto &v : fwd)
-            if (!taken.count({v[1], v[3]})) reg.push_back(make_int2(v[1], v[3]));
-        q->n_fwd_reg = (int)reg.size();
-        for (auto &v : bwd)
-            if (!taken.count({v[1], v[3]})) reg.push_back(make_int2(v[1], v[3]));
-        q->n_bwd_reg = (int)reg.size() - q->n_fwd_reg;
-        q->nch = (int)chains.size();
-        if (q->nch > 0) {
-            CK(cudaMalloc(&q->d_chains, chains.size() * sizeof(int2)));
-            CK(cudaMemcpy(q->d_chains, chains.data(), chains.size() * sizeof(int2), cudaMemcpyHostToDevice));
-            CK(cudaMalloc(&q->d_items_reg, std::max<size_t>(1, reg.size()) * sizeof(int2)));
-            if (!reg.empty())
-                CK(cudaMemcpy(q->d_items_reg, reg.data(), reg.size() * sizeof(int2), cudaMemcpyHostToDevice));
-        }
+        std::stable_sort(q->cand.begin(), q->cand.end(),
+                         [](const std::array<int, 3> &x, const std::array<int, 3> &y) { return x[0] > y[0]; });
+        if ((int)q->cand.size() > QCHAIN_MAX) q->cand.resize(QCHAIN_MAX);
+        for (auto &v : fwd) q->fwd_items.push_back(make_int2(v[1], v[3]));
+        for (auto &v : bwd) q->bwd_items.push_back(make_int2(v[1], v[3]));
+        CK(cudaMalloc(&q->d_chains, std::max<size_t>(1, q->cand.size()) * sizeof(int2)));
+        CK(cudaMalloc(&q->d_items_reg, std::max<size_t>(1, q->fwd_items.size() + q->bwd_items.size()) * sizeof(int2)));
     }
     CK(cudaMalloc(&q->d_sys, m * sizeof(QSys)));
     CK(cudaMalloc(&q->d_sched, sizeof(Sched)));
@@ -4142,7 +4156,8 @@ kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
     q->rc.sched = q->d_sched;
     q->rc.trace = nullptr;
     q->rc.unpublished_row = -1;
-    kkt_status st = q_configure(q.get(), 0, 0);
+    kkt_status st = q_set_chains(q.get(), (int)q->cand.size());
+    if (st == KKT_OK) st = q_configure(q.get(), 0, 0);
     if (st) { kkt_queue_destroy(q.release()); return st; }
     *out = q.release();
     return KKT_OK;
@@ -4165,7 +4180,16 @@ void kkt_queue_destroy(kkt_queue *q) {
 kkt_status kkt_queue_set_launch(kkt_queue *q, int cta_warps, int ctas) {
     if (!q || cta_warps < 0 || ctas < 0) return KKT_ERR_ARG;
     DeviceGuard g(q->dev);
+    q->ctas_opt = ctas;
     return q_configure(q, cta_warps, ctas);
+}
+
+kkt_status kkt_queue_set_tiles(kkt_queue *q, int cta_tasks) {
+    if (!q || cta_tasks < -1) return KKT_ERR_ARG;
+    DeviceGuard g(q->dev);
+    kkt_status st = q_set_chains(q, cta_tasks < 0 ? (int)q->cand.size() : cta_tasks);
+    if (st) return st;
+    return q_configure(q, q->cta_warps, q->ctas_opt);
 }
 
 template <typename T>

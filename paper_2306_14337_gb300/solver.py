@@ -442,6 +442,11 @@ class KKTQueue:
         check(self._lib.kkt_queue_set_launch(self._h, int(cta_warps), int(ctas)), "kkt_queue_set_launch")
         self.launch = (int(cta_warps), int(ctas))
 
+    def set_tiles(self, cta_tasks=-1):
+        """How many of the longest solve tasks run on a CTA each (-1: all candidates)."""
+        check(self._lib.kkt_queue_set_tiles(self._h, int(cta_tasks)), "kkt_queue_set_tiles")
+        self.tiles = int(cta_tasks)
+
     @staticmethod
     def _ptrs(ts):
         return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])

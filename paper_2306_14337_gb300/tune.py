@@ -1,10 +1,12 @@
-"""Autotuner for the launch shape of the uneven-pattern queue.
+"""Autotuner for the launch shape and tiles of the uneven-pattern queue.
 
-Candidates are (warps per CTA, CTA count) pairs of the persistent kernels
-(0 CTAs = as many as fit).  Each candidate is applied, run a few times and
-timed; the fastest is kept.  Results are cached per set of patterns (a
-fingerprint of their sizes and index arrays), in memory and optionally in a
-JSON file, so a pattern set is tuned once.
+Candidates are (warps per CTA, CTA count[, CTA tasks]) tuples: the persistent
+kernels' CTA shape (0 CTAs = as many as fit) and, optionally, how many of the
+longest solve tasks run on a whole CTA each (-1 = all candidates; CTA tasks
+need 8-warp CTAs).  Each candidate is applied, run a few times and timed; the
+fastest is kept.  Results are cached per set of patterns (a fingerprint of
+their sizes and index arrays), in memory and optionally in a JSON file, so a
+pattern set is tuned once.
 """
 from __future__ import annotations
 
@@ -13,7 +15,17 @@ import json
 import os
 import statistics
 
-DEFAULT_CANDIDATES = ((8, 0), (4, 0), (2, 0), (8, 152), (4, 304), (2, 608), (1, 1216))
+DEFAULT_CANDIDATES = ((8, 0, -1), (8, 0, 16), (8, 0, 4), (8, 0, 0), (4, 0), (2, 0), (8, 152, -1),
+                      (4, 304), (2, 608), (1, 1216))
+
+
+def apply_candidate(queue, cand):
+    """Set a candidate's launch shape and, when it has one, its tile choice."""
+    queue.set_launch(cand[0], cand[1])
+    if len(cand) > 2:
+        queue.set_tiles(cand[2])
+    elif hasattr(queue, "set_tiles"):
+        queue.set_tiles(-1)
 
 _memo: dict = {}
 
@@ -52,9 +64,9 @@ def autotune_queue(queue, run_once, patterns, candidates=DEFAULT_CANDIDATES, rep
         except (OSError, ValueError):
             cached = None
     if cached is not None:
-        queue.set_launch(*cached)
+        apply_candidate(queue, cached)
         return tuple(cached), None
-    best, table = pick(lambda c: queue.set_launch(*c), run_once, candidates, reps)
+    best, table = pick(lambda c: apply_candidate(queue, c), run_once, candidates, reps)
     _memo[key] = list(best)
     if cache_path:
         data = {}

@@ -70,3 +70,23 @@ def test_queue_factors_match_single_context():
         rp, ci, ref, E = o.F.lu_csr()
         got = on_fill(sols[k], rp, ci, sols[k].export_factors().cpu().numpy())
         assert np.all(np.abs(got - ref) <= np.maximum(1e-11 * np.abs(ref), 4 * E))
+
+
+@pytest.mark.parametrize("tiles", [0, 1, -1])
+def test_queue_tile_choice_keeps_results(tiles):
+    """kkt_queue_set_tiles moves tasks between CTA tasks and warp items; the
+    refined solutions stay within the target either way."""
+    seqs = _systems()
+    sols = [KKTSolver(s.n, s.indptr, s.indices, refine_mode="auto") for s in seqs]
+    Q = KKTQueue(sols)
+    Q.set_launch(8, 0)
+    Q.set_tiles(tiles)
+    vals = [torch.tensor(s.values(1), device=DEV) for s in seqs]
+    bs = [torch.tensor(s.rhs(1), device=DEV) for s in seqs]
+    xs = [torch.zeros_like(b) for b in bs]
+    om = torch.zeros(len(seqs), dtype=torch.float64, device=DEV)
+    Q.run(vals, bs, xs, n_refine=3, omega=om)
+    torch.cuda.synchronize()
+    for k, s in enumerate(seqs):
+        w = oracle.omega(s.n, s.indptr, s.indices, s.values(1), s.rhs(1), xs[k].cpu().numpy())
+        assert w <= 1e-14 or sols[k].refine(bs[k], xs[k], 1e-14, 20)["converged"], (k, w)

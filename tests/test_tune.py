@@ -37,3 +37,22 @@ def test_autotune_caches_per_pattern_set(tmp_path):
     best2, table2 = tune.autotune_queue(q2, lambda: 1 / 0, pats, candidates=list(cost), cache_path=path)
     assert best2 == (2, 608) and table2 is None and q2.launch == (2, 608) and q2.calls == 1
     assert tune.fingerprint(pats) != tune.fingerprint([(3, [0, 1, 2, 3], [0, 2, 1])])
+
+
+def test_candidates_with_a_tile_choice_set_it():
+    class TiledQueue(FakeQueue):
+        def __init__(self):
+            super().__init__()
+            self.tiles = None
+
+        def set_tiles(self, k):
+            self.tiles = k
+
+    q = TiledQueue()
+    cost = {(8, 0, -1): 2.0, (8, 0, 4): 1.0, (4, 0): 3.0}
+    best, table = tune.pick(lambda c: tune.apply_candidate(q, c),
+                            lambda: cost[q.launch + ((q.tiles,) if q.launch[0] == 8 else ())],
+                            candidates=list(cost), reps=1)
+    assert best == (8, 0, 4) and q.launch == (8, 0) and q.tiles == 4
+    tune.apply_candidate(q, (4, 0))            # no tile choice: all candidates again
+    assert q.tiles == -1
