@@ -335,7 +335,7 @@ cudaError_t dense_lu_prepare(int fp32, int s, int sms, int *ctas) {
         fn = (const void *)k_dense_lu<double, 16>;
         smem = dn_smem<double, 16>(s);
     }
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
     int per = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, DTHREADS, smem);

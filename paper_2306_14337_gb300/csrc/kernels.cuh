@@ -146,6 +146,10 @@ int dense_lu_max_rows(int fp32);
 size_t dense_lu_ctl_bytes(int s);
 cudaError_t dense_lu_prepare(int fp32, int s, int sms, int *ctas);
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` (never lowers it; thread-safe).
+cudaError_t ensure_smem(const void *f, size_t bytes);
+
 // Record the text returned by kkt_last_error() on the calling thread (every
 // translation unit of the library reports through this one store).
 void set_last_error(const std::string &msg);

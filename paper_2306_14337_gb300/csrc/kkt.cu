@@ -2444,11 +2444,13 @@ inline int blocks_for(long long threads, int bs) { return (int)((threads + bs - 
 // grid-stride beyond 2,048 CTAs, so the per-CTA atomics stay few
 inline int norm_blocks(long long n) { return std::max(1, std::min(blocks_for(8 * n, RTHREADS), 2048)); }
 
+}  // namespace
+
 // Raise a kernel's dynamic shared-memory limit on the current device to at
 // least `bytes`.  The limit belongs to the kernel, not to a context, so it is
 // only ever raised: a context created later with smaller needs must not break
 // the launches of one created earlier.
-cudaError_t ensure_smem(const void *f, size_t bytes) {
+cudaError_t kkt::ensure_smem(const void *f, size_t bytes) {
     static std::mutex m;
     static std::map<std::pair<const void *, int>, size_t> done;
     int dev = 0;
@@ -2461,7 +2463,6 @@ cudaError_t ensure_smem(const void *f, size_t bytes) {
     if (e == cudaSuccess) have = bytes;
     return e;
 }
-}  // namespace
 
 // The entry points below have C linkage through their declarations in kkt.h.
 

@@ -230,3 +230,19 @@ def test_dense_block_with_value_aware_row_permutation():
     info = S.refine(_t(b), x, 1e-14, 20)
     assert info["converged"], info
     assert oracle.omega(s.n, s.indptr, s.indices, v, b, x.cpu().numpy()) <= 1e-14
+
+
+def test_dense_blocks_of_different_sizes_coexist():
+    """k_dense_lu's shared-memory limit belongs to the kernel: a context with a
+    smaller block created after one with a larger block must not break the
+    larger one's launches."""
+    s = config_sequence(1)
+    p = _perm("cfg1", s.n, s.indptr, s.indices)
+    v = s.values(3)
+    big = KKTSolver(s.n, s.indptr, s.indices, perm=p, fp32=True, dense_block=400)
+    small = KKTSolver(s.n, s.indptr, s.indices, perm=p, fp32=True, dense_block=40)
+    assert big.stats()["dense_rows"] == 400 and small.stats()["dense_rows"] == 40
+    o = oracle.Oracle(s.n, s.indptr, s.indices, v, p, tau_rel=2.0 ** -24)
+    for S in (small, big):
+        S.refactor(_t(v))
+        _check(S, o, True)
