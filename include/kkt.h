@@ -145,6 +145,17 @@ typedef struct {
                                lowers the scaled residual to at most this fraction of
                                the previous one, then FGMRES takes over (0: 0.5; must
                                be below 1) */
+    int solve_far_blocks;   /* triangular solves: a row of a long task (one run by a
+                               whole CTA) whose sources in its own task lie more than
+                               this many 32-row blocks back -- at least 32 of them --
+                               has their sum computed by a partner CTA of the task,
+                               which streams those entries on another SM as the
+                               task's CTA publishes the rows; the task's CTA then
+                               reads only the last blocks' entries of such a row.
+                               0: 2 blocks; -1: off. */
+    int solve_far_ctas;     /* partner CTAs of the single-system solves, given to the
+                               long tasks with the most far entries (0: 8; -1: none;
+                               at most a third of the CTAs left after the long tasks) */
 } kkt_options;
 
 typedef struct {
@@ -175,6 +186,9 @@ typedef struct {
     int refactor_big_cap;   /* row capacity (entries) of those warps' shared memory */
     int dense_rows;         /* rows of the dense root block (0: none) */
     int refactor_row_cap;   /* row buffer entries of the refactorization's warps */
+    int solve_far_rows;     /* rows of long solve tasks whose far sources in their own
+                               task a partner CTA sums (forward phase) */
+    int solve_far_ctas;     /* partner CTAs of the single-system solves */
 } kkt_stats;
 
 typedef struct {

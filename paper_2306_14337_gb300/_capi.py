@@ -55,6 +55,8 @@ class Options(C.Structure):
         ("dense_block", C.c_int),
         ("refactor_row_cap", C.c_int),
         ("refine_auto_ratio", C.c_double),
+        ("solve_far_blocks", C.c_int),
+        ("solve_far_ctas", C.c_int),
     ]
 
 
@@ -86,6 +88,8 @@ class Stats(C.Structure):
         ("refactor_big_cap", C.c_int),
         ("dense_rows", C.c_int),
         ("refactor_row_cap", C.c_int),
+        ("solve_far_rows", C.c_int),
+        ("solve_far_ctas", C.c_int),
     ]
 
 

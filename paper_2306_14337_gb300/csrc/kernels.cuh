@@ -99,6 +99,17 @@ struct TaskCfg {
     const int *ext_rows;
     const int *cs_ext;
     void *ext;
+    // Far sources of CTA-task rows (optional, far != null): CTAs nchain ..
+    // nchain + npart - 1 are partners; partner p sums, for the far rows
+    // far_rows[part[p].x + r] (r = part[p].z * warps + warp, stepping by
+    // part[p].w * warps, r < part[p].y), the slots between cs_ext[row] and
+    // cs_far[row] (forward: [cs_ext, cs_far), backward: [cs_far, cs_ext)) and
+    // publishes the sum in far[row].
+    int npart;
+    const int4 *part;
+    const int *far_rows;
+    const int *cs_far;
+    void *far;
 };
 
 struct RunCfg {

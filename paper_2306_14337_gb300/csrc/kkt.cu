@@ -1358,6 +1358,11 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
             if (BACKWARD) { outside = ce < q.w; q.w = ce; }
             else { outside = ce > q.x; q.x = ce; }
         }
+        if (tk.far) {                       // bit 1: far sources summed by a partner
+            const int cf = tk.cs_far[i];
+            if (BACKWARD) { if (cf < q.w) { outside |= 2; q.w = cf; } }
+            else if (cf > q.x) { outside |= 2; q.x = cf; }
+        }
         q.y = tk.cs_late[i];
         q.z = tk.cs_diag[i];
         if (BACKWARD) base = yin[i];
@@ -1608,13 +1613,17 @@ __device__ __forceinline__ void trisolve_chain(const DevPattern &P, const RunCfg
             int outside = 0;
             if (own) {
                 meta(k0 + lane, mt, base, scl);
-                outside = ext ? outside_of(k0 + lane) : 0;
+                outside = (ext || tk.far) ? outside_of(k0 + lane) : 0;
             }
-            // the outside sum published by its item (polled; all lanes take part)
-            const T xo = warp_wait_load(rc, ext + (outside ? row_of(k0 + lane) : 0), outside != 0, lane);
+            // the outside sum published by its item and the far sum by a
+            // partner (polled; all lanes take part)
+            const T xo = warp_wait_load(rc, ext + ((outside & 1) ? row_of(k0 + lane) : 0), (outside & 1) != 0, lane);
+            const T *farp = reinterpret_cast<const T *>(tk.far);
+            const T xf = warp_wait_load(rc, farp + ((outside & 2) ? row_of(k0 + lane) : 0), (outside & 2) != 0, lane);
             if (own) {
                 T e = (sub[lane] + sub[CB + lane]) + (sub[2 * CB + lane] + sub[3 * CB + lane]);
-                if (outside) e += xo;
+                if (outside & 1) e += xo;
+                if (outside & 2) e += xf;
                 xbb[lane] = FOLD ? (base - e) * scl : base - e;
             }
         }
@@ -1749,16 +1758,13 @@ __device__ __forceinline__ void trisolve_pack(const DevPattern &P, const RunCfg 
     }
 }
 
-// The outside part of one row of a CTA task: the sum over its dependencies
-// in other tasks (a warp per row, loads first, next chunk in flight), published
-// for the row's CTA.  Runs on warps anywhere on the GPU, so the long paths'
-// CTAs only stream their own entries.
-template <typename T, bool BACKWARD>
-__device__ __forceinline__ void trisolve_ext(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
-                                             const T *__restrict__ F, T *yout, int i, int lane) {
+// The sum over the slots [tb, te) of one row, F[t] times the published value
+// of source lu_ci[t] (a warp per row, loads first, next chunk in flight,
+// waiting on sources not yet published); every lane returns the sum.
+template <typename T>
+__device__ __forceinline__ T trisolve_sum(const DevPattern &P, const RunCfg &rc, const T *__restrict__ F,
+                                          const T *yout, int tb, int te, int lane) {
     constexpr int Q = 8;
-    const int tb = BACKWARD ? tk.cs_ext[i] : P.lu_rp[i];
-    const int te = BACKWARD ? P.lu_rp[i + 1] : tk.cs_ext[i];
     auto load = [&](int t0, int (&c)[Q], T (&f)[Q]) {
 #pragma unroll
         for (int q = 0; q < Q; q++) {
@@ -1806,8 +1812,36 @@ __device__ __forceinline__ void trisolve_ext(const DevPattern &P, const RunCfg &
             f1[q] = f2[q];
         }
     }
-    acc = warp_sum(acc);
+    return warp_sum(acc);
+}
+
+// The outside part of one row of a CTA task: the sum over its dependencies
+// in other tasks, published for the row's CTA.  Runs on warps anywhere on the
+// GPU, so the long paths' CTAs only stream their own entries.
+template <typename T, bool BACKWARD>
+__device__ __forceinline__ void trisolve_ext(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
+                                             const T *__restrict__ F, T *yout, int i, int lane) {
+    const int tb = BACKWARD ? tk.cs_ext[i] : P.lu_rp[i];
+    const int te = BACKWARD ? P.lu_rp[i + 1] : tk.cs_ext[i];
+    const T acc = trisolve_sum<T>(P, rc, F, yout, tb, te, lane);
     if (lane == 0) publish(rc, reinterpret_cast<T *>(tk.ext) + i, acc);
+}
+
+// A partner CTA of a CTA task: its warps sum the far sources of the task's far
+// rows (those more than a few blocks back in the task), row after row in step
+// order, each waiting in global memory for the rows the task's CTA publishes.
+template <typename T, bool BACKWARD>
+__device__ __forceinline__ void trisolve_partner(const DevPattern &P, const RunCfg &rc, const TaskCfg &tk,
+                                                 const T *__restrict__ F, const T *yout, int p, int wid,
+                                                 int nw, int lane) {
+    const int4 pt = tk.part[p];
+    for (int r = pt.z * nw + wid; r < pt.y; r += pt.w * nw) {
+        const int i = tk.far_rows[pt.x + r];
+        const int tb = BACKWARD ? tk.cs_far[i] : tk.cs_ext[i];
+        const int te = BACKWARD ? tk.cs_ext[i] : tk.cs_far[i];
+        const T acc = trisolve_sum<T>(P, rc, F, yout, tb, te, lane);
+        if (lane == 0) publish(rc, reinterpret_cast<T *>(tk.far) + i, acc);
+    }
 }
 
 // Packs, once per refactorization, the tiles the CTA tasks of the four solve
@@ -1874,6 +1908,11 @@ k_trisolve(DevPattern P, RunCfg rc, TaskCfg tk, const T *__restrict__ F, const T
         trisolve_chain<T, BACKWARD, TRANS>(P, rc, tk, blockIdx.x, tk.task_lo[tid], tk.task_hi[tid], F, rcp, rhs, sp,
                                            yin, yout, out, accumulate, smem);
         if (wid == 0) trace_mark(rc, tbase, item, 1, lane);
+        if (lane == 0) finish_launch(rc, e);
+        return;
+    }
+    if ((int)blockIdx.x < tk.nchain + tk.npart) {  // a partner of a CTA task
+        trisolve_partner<T, BACKWARD>(P, rc, tk, F, yout, (int)blockIdx.x - tk.nchain, wid, blockDim.x >> 5, lane);
         if (lane == 0) finish_launch(rc, e);
         return;
     }
@@ -2370,6 +2409,11 @@ struct kkt_ctx {
     std::vector<int> chain_h;        // CTA tasks of the single-system solves (host copy)
     // outside items of CTA-task rows: splits and rows per direction, order lengths
     const int *ce_fwd = nullptr, *ce_bwd = nullptr, *xr_fwd = nullptr, *xr_bwd = nullptr;
+    // far sources of CTA-task rows summed by partner CTAs: slot bounds, far
+    // rows in step order, partner tables (see the task setup in upload)
+    const int *cf_fwd = nullptr, *cf_bwd = nullptr, *fr_fwd = nullptr, *fr_bwd = nullptr;
+    const int4 *part_fwd = nullptr, *part_bwd = nullptr;
+    int npart = 0;
     int nord_f = 0, nord_b = 0;
     size_t solve_smem = 0, bsolve_smem = 0;
     unsigned long long *h_norms = nullptr;  // pinned
@@ -2394,6 +2438,7 @@ struct kkt_ctx {
     int *d_dense_ctl = nullptr;      // k_dense_lu: a published flag per block column
     int dense_ld = 0, dense_grid = 0;   // dense_grid: CTAs (block columns) of k_dense_lu
     int cap_r = 0;                   // row capacity of k_refactor's small warps
+    int far_rows = 0;                // rows of CTA solve tasks whose far sources a partner sums
     bool factored = false;
     int last_iters = 0;
     double last_omega = -1.0;
@@ -2495,6 +2540,8 @@ void kkt_default_options(kkt_options *o) {
     o->dense_block = 0;
     o->refactor_row_cap = 0;
     o->refine_auto_ratio = 0.0;
+    o->solve_far_blocks = 0;
+    o->solve_far_ctas = 0;
 }
 
 const char *kkt_status_string(kkt_status s) {
@@ -2592,7 +2639,7 @@ static kkt_status upload(kkt_ctx *c) {
     CK(cudaMalloc(&c->d_s, n * sizeof(double)));
     CK(cudaMalloc(&c->d_sp, n * sizeof(double)));
     CK(cudaMalloc(&c->d_rho, n * sizeof(double)));
-    CK(cudaMalloc(&c->d_y, 4 * (size_t)n * sizeof(double)));   // y, z, outside sums (forward, backward)
+    CK(cudaMalloc(&c->d_y, 6 * (size_t)n * sizeof(double)));   // y, z, outside sums, far sums (fwd, bwd)
     CK(cudaMalloc(&c->d_status, ST_WORDS * sizeof(int)));
     CK(cudaMalloc(&c->d_norms, NM_WORDS * sizeof(unsigned long long)));
     CK(cudaMalloc(&c->d_sched, sizeof(Sched)));
@@ -2804,21 +2851,59 @@ static kkt_status upload(kkt_ctx *c) {
         // forward by the row's depth among the depth-ordered tasks (its outside
         // sources are deeper), backward right after its task's position (its
         // outside sources are ancestors in earlier tasks).
-        std::vector<int> ce_f(n, 0), ce_b(n, 0), xr_f, xr_b;
+        // Far sources (forward / backward phases alike): a row's sources in its
+        // own task more than `far` blocks back, if there are at least FAR_MIN
+        // of them, are summed by a partner CTA of the task (a CTA of its own,
+        // streaming those entries on another SM while the task's CTA walks on)
+        // and published in a per-row array; the task's CTA then reads only the
+        // entries of the last blocks.  A partner's warps take the task's far
+        // rows in step order and wait only for rows at least `far` blocks
+        // back, which the task's CTA produces without them, so every wait ends.
+        const int far = c->opt.solve_far_blocks < 0 ? 0 : (c->opt.solve_far_blocks == 0 ? 2
+                                                                                         : c->opt.solve_far_blocks);
+        constexpr int FAR_MIN = 32;
+        std::vector<int> ce_f(n, 0), ce_b(n, 0), cf_f(n, 0), cf_b(n, 0), xr_f, xr_b;
+        std::vector<int> fr_f, fr_b;                       // far rows of each CTA task, in step order
+        std::vector<int> fo_f(chain.size() + 1, 0), fo_b(chain.size() + 1, 0);
+        std::vector<double> far_load(chain.size(), 0.0);   // far entries of each CTA task
         {
             std::vector<int> task_of_row(n, -1);
             for (int T : chain)
                 for (int i = a.task_lo[T]; i <= a.task_hi[T]; i++) task_of_row[i] = T;
             const int *ci = a.lu_ci.data();
-            for (int T : chain) {
-                const int lo = a.task_lo[T], hi = a.task_hi[T];
+            for (size_t qc = 0; qc < chain.size(); qc++) {
+                const int T = chain[qc], lo = a.task_lo[T], hi = a.task_hi[T];
                 for (int i = lo; i <= hi; i++) {
-                    const int rb = a.lu_rp[i], dg = a.diag[i], re = a.lu_rp[i + 1];
-                    ce_f[i] = (int)(std::lower_bound(ci + rb, ci + dg, lo) - ci);
-                    ce_b[i] = (int)(std::upper_bound(ci + dg + 1, ci + re, hi) - ci);
+                    const int rb = a.lu_rp[i], dg = a.diag[i];
+                    ce_f[i] = cf_f[i] = (int)(std::lower_bound(ci + rb, ci + dg, lo) - ci);
+                    const int bf = (i - lo) / CB;
+                    if (far > 0 && bf > far) {
+                        const int e = (int)(std::lower_bound(ci + rb, ci + dg, lo + CB * (bf - far)) - ci);
+                        if (e - ce_f[i] >= FAR_MIN) {
+                            cf_f[i] = e;
+                            fr_f.push_back(i);
+                            far_load[qc] += e - ce_f[i];
+                        }
+                    }
                     if (ce_f[i] > rb) xr_f.push_back(i);
-                    if (ce_b[i] < re) xr_b.push_back(i);
                 }
+                fo_f[qc + 1] = (int)fr_f.size();
+                for (int i = hi; i >= lo; i--) {
+                    const int dg = a.diag[i], re = a.lu_rp[i + 1];
+                    ce_b[i] = cf_b[i] = (int)(std::upper_bound(ci + dg + 1, ci + re, hi) - ci);
+                    const int bb = (hi - i) / CB;
+                    if (far > 0 && bb > far) {
+                        const int e = (int)(std::upper_bound(ci + dg + 1, ci + re, hi - CB * (bb - far)) - ci);
+                        if (ce_b[i] - e >= FAR_MIN) {
+                            cf_b[i] = e;
+                            fr_b.push_back(i);
+                            far_load[qc] += ce_b[i] - e;
+                        }
+                    }
+                }
+                for (int i = lo; i <= hi; i++)
+                    if (ce_b[i] < a.lu_rp[i + 1]) xr_b.push_back(i);
+                fo_b[qc + 1] = (int)fr_b.size();
             }
             // forward: merge into the depth-ordered part after the prefix and packs
             const size_t head = (size_t)nlong1 + (pack_rows.size() / 32);
@@ -2845,6 +2930,42 @@ static kkt_status upload(kkt_ctx *c) {
             ob1.clear();
             for (auto &e : bk) ob1.push_back(e[2]);
         }
+        // Partner CTAs: up to `nfar` CTAs (at most a third of the CTAs left
+        // after the CTA tasks), each given to the task with the most far
+        // entries per partner; a task left without one keeps its far sources.
+        std::vector<int> parts(chain.size(), 0);
+        {
+            const int want = c->opt.solve_far_ctas < 0 ? 0 : (c->opt.solve_far_ctas == 0 ? 8 : c->opt.solve_far_ctas);
+            const int nfar = std::max(0, std::min(want, (c->solve_grid - (int)chain.size()) / 3));
+            for (int k = 0; k < nfar; k++) {
+                int best = -1;
+                double bl = 0.0;
+                for (size_t qc = 0; qc < chain.size(); qc++) {
+                    const double l = far_load[qc] / (parts[qc] + 1);
+                    if (l > bl) { bl = l; best = (int)qc; }
+                }
+                if (best < 0) break;
+                parts[best]++;
+            }
+        }
+        std::vector<int> part_f, part_b, fr_f2, fr_b2;
+        c->far_rows = 0;
+        for (size_t qc = 0; qc < chain.size(); qc++) {
+            if (parts[qc] == 0) {                       // no partner: the CTA sums every source in its task
+                for (int k = fo_f[qc]; k < fo_f[qc + 1]; k++) cf_f[fr_f[k]] = ce_f[fr_f[k]];
+                for (int k = fo_b[qc]; k < fo_b[qc + 1]; k++) cf_b[fr_b[k]] = ce_b[fr_b[k]];
+                continue;
+            }
+            const int of0 = (int)fr_f2.size(), ob0 = (int)fr_b2.size();
+            fr_f2.insert(fr_f2.end(), fr_f.begin() + fo_f[qc], fr_f.begin() + fo_f[qc + 1]);
+            fr_b2.insert(fr_b2.end(), fr_b.begin() + fo_b[qc], fr_b.begin() + fo_b[qc + 1]);
+            c->far_rows += fo_f[qc + 1] - fo_f[qc];
+            for (int r = 0; r < parts[qc]; r++) {
+                part_f.insert(part_f.end(), {of0, fo_f[qc + 1] - fo_f[qc], r, parts[qc]});
+                part_b.insert(part_b.end(), {ob0, fo_b[qc + 1] - fo_b[qc], r, parts[qc]});
+            }
+        }
+        c->npart = (int)part_f.size() / 4;
         std::vector<int> blk0(chain.size() + 1, 0), binfo;
         for (size_t q = 0; q < chain.size(); q++) {
             const int T = chain[q], nbq = (len[T] + CB - 1) / CB;
@@ -2888,7 +3009,8 @@ static kkt_status upload(kkt_ctx *c) {
         int *d = nullptr;
         const size_t words = 3 * (size_t)nt + 3 * (size_t)(nt + xr_f.size() + xr_b.size()) + chain.size() +
                              4 * (size_t)n + blk0.size() + binfo.size() + pack_rows.size() + 2 * (size_t)n +
-                             xr_f.size() + xr_b.size();
+                             xr_f.size() + xr_b.size() + 2 * (size_t)n + fr_f2.size() + fr_b2.size() +
+                             part_f.size() + part_b.size() + 4;
         CK(cudaMalloc(&d, words * sizeof(int)));
         size_t o = 0;
         auto put = [&](const std::vector<int> &v) -> const int * {
@@ -2920,6 +3042,13 @@ static kkt_status upload(kkt_ctx *c) {
         c->ce_bwd = put(ce_b);
         c->xr_fwd = put(xr_f);
         c->xr_bwd = put(xr_b);
+        c->cf_fwd = put(cf_f);
+        c->cf_bwd = put(cf_b);
+        c->fr_fwd = put(fr_f2);
+        c->fr_bwd = put(fr_b2);
+        o = (o + 3) & ~(size_t)3;                       // int4 tables: 16-byte aligned
+        c->part_fwd = reinterpret_cast<const int4 *>(put(part_f));
+        c->part_bwd = reinterpret_cast<const int4 *>(put(part_b));
         c->nord_f = (int)of1.size();
         c->nord_b = (int)ob1.size();
         c->tk1.ext_base = nt;
@@ -3131,7 +3260,8 @@ static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, con
         c->opt.jacobi_sweeps < 0 || c->opt.dense_block < -1 || c->opt.refactor_row_cap < 0 ||
         !(c->opt.refine_auto_ratio >= 0.0 && c->opt.refine_auto_ratio < 1.0) ||
         c->opt.max_batch < 1 || c->opt.cta_warps < 0 || c->opt.refactor_ctas < 0 ||
-        c->opt.solve_ctas < 0) {
+        c->opt.solve_ctas < 0 || c->opt.solve_far_blocks < -1 ||
+        c->opt.solve_far_ctas < -1) {
         g_last_error = "invalid option";
         return KKT_ERR_ARG;
     }
@@ -3303,6 +3433,11 @@ static TaskCfg tasks_of(const kkt_ctx *c, bool backward, bool trans) {
         const size_t tsz_ = c->opt.factor_fp32 ? sizeof(float) : sizeof(double);
         const size_t n = (size_t)c->an.n;
         t.ext = (char *)c->d_y + (2 + (backward ? 1 : 0)) * n * tsz_;
+        t.npart = c->npart;
+        t.part = backward ? c->part_bwd : c->part_fwd;
+        t.far_rows = backward ? c->fr_bwd : c->fr_fwd;
+        t.cs_far = backward ? c->cf_bwd : c->cf_fwd;
+        t.far = c->npart ? (char *)c->d_y + (4 + (backward ? 1 : 0)) * n * tsz_ : nullptr;
     }
     const int ph = (trans ? 2 : 0) + (backward ? 1 : 0);
     const size_t tsz = c->opt.factor_fp32 ? sizeof(float) : sizeof(double);
@@ -3316,7 +3451,7 @@ static kkt_status launch_solve(kkt_ctx *c, const double *b, double *x, int accum
     const int n = c->an.n;
     T *y = (T *)c->d_y, *z = y + n;
     const T *L = (const T *)c->d_lu, *R = (const T *)c->d_rcp;
-    CK(cudaMemsetAsync(y, 0xff, 4 * (size_t)n * sizeof(T), s));   // y, z and the outside sums
+    CK(cudaMemsetAsync(y, 0xff, (c->npart ? 6 : 4) * (size_t)n * sizeof(T), s));   // y, z, outside and far sums
     k_trisolve<T, false, false><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
         c->P, c->rc, tasks_of(c, false, false), L, R, b, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
@@ -3334,7 +3469,7 @@ static kkt_status launch_solve_t(kkt_ctx *c, const double *g, double *lam, int a
     const int n = c->an.n;
     T *y = (T *)c->d_y, *z = y + n;
     const T *L = (const T *)c->d_lut, *R = (const T *)c->d_rcp;
-    CK(cudaMemsetAsync(y, 0xff, 4 * (size_t)n * sizeof(T), s));   // y, z and the outside sums
+    CK(cudaMemsetAsync(y, 0xff, (c->npart ? 6 : 4) * (size_t)n * sizeof(T), s));   // y, z, outside and far sums
     k_trisolve<T, false, true><<<c->solve_grid, c->solve_warps * 32, c->solve_smem, s>>>(
         c->P, c->rc, tasks_of(c, false, true), L, R, g, c->d_sp, nullptr, y, nullptr, 0);
     CK(cudaGetLastError());
@@ -4150,6 +4285,8 @@ kkt_status kkt_queue_create(kkt_ctx *const *ctxs, int m, kkt_queue **out) {
         for (int ph = 0; ph < 4; ph++) {
             s.tkc[ph] = tasks_of(c, ph & 1, ph >= 2);
             s.tkc[ph].ext = nullptr;           // a queue's CTA tasks sum their outside parts themselves
+            s.tkc[ph].far = nullptr;           // and their far sources
+            s.tkc[ph].npart = 0;
         }
     }
     q->rc = ctxs[0]->rc;
@@ -4491,6 +4628,8 @@ kkt_status kkt_get_stats(const kkt_ctx *c, kkt_stats *o) {
     o->max_task = a.max_task;
     o->dense_rows = a.dense_rows;
     o->refactor_row_cap = c->cap_r;
+    o->solve_far_rows = c->far_rows;
+    o->solve_far_ctas = c->npart;
     return KKT_OK;
 }
 

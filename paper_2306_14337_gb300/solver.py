@@ -50,7 +50,8 @@ class KKTSolver:
                  pivot_tau_rel=0.0, spin_limit=4_000_000, cta_warps=0, refactor_ctas=0,
                  solve_ctas=0, update_map_budget=0, trace=False, max_batch=1, unpublished_row=-1,
                  poll_ns_max=0, refactor_big_warps=0, symmetric=False, jacobi_sweeps=8, values=None,
-                 row_perm=None, dense_block=0, refactor_row_cap=0, refine_auto_ratio=0.0, device=0):
+                 row_perm=None, dense_block=0, refactor_row_cap=0, refine_auto_ratio=0.0,
+                 solve_far_blocks=0, solve_far_ctas=0, device=0):
         self._lib = _capi.load()
         self.n = int(n)
         self._rp = _i32(indptr)
@@ -84,6 +85,8 @@ class KKTSolver:
         opt.dense_block = int(dense_block)
         opt.refactor_row_cap = int(refactor_row_cap)
         opt.refine_auto_ratio = float(refine_auto_ratio)
+        opt.solve_far_blocks = int(solve_far_blocks)
+        opt.solve_far_ctas = int(solve_far_ctas)
         self._row_perm = None
         if row_perm is not None:
             self._row_perm = _i32(row_perm)

@@ -283,3 +283,17 @@ def test_dense_root_block_off_and_bad_option():
     with pytest.raises(KKTError) as ei:
         KKTSolver(s.n, s.indptr, s.indices, dense_block=-2, device=None)
     assert ei.value.status == _capi.KKT_ERR_ARG
+
+
+def test_far_source_options_validated():
+    """solve_far_blocks / solve_far_ctas accept -1 (off), 0 (default) and
+    positive values; anything below -1 is refused.  A host-only context runs
+    no solve, so it reports no partner CTAs."""
+    s = config_sequence(0)
+    S = KKTSolver(s.n, s.indptr, s.indices, solve_far_blocks=2, solve_far_ctas=3, device=None)
+    st = S.stats()
+    assert st["solve_far_ctas"] == 0 and st["solve_far_rows"] == 0
+    for kw in (dict(solve_far_blocks=-2), dict(solve_far_ctas=-2)):
+        with pytest.raises(KKTError) as ei:
+            KKTSolver(s.n, s.indptr, s.indices, device=None, **kw)
+        assert ei.value.status == _capi.KKT_ERR_ARG

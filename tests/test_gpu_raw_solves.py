@@ -119,3 +119,40 @@ def test_raw_solves_70000bus_fp32_full_size():
     S = KKTSolver(s.n, s.indptr, s.indices, fp32=True)
     S.refactor(_t(s.values(0)))
     _check(S, s.rhs(0), True)
+
+
+@pytest.mark.parametrize("far_blocks,far_ctas", [(1, 0), (3, 1), (1, 6), (-1, 0), (3, -1)])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_raw_solves_far_sources_on_partner_ctas(far_blocks, far_ctas, fp32):
+    """Long solve tasks hand the sums over their own sources more than a few
+    blocks back to partner CTAs (Algorithm 2's dependency-driven substitution
+    with the far part of a row summed on another SM).  Every split -- one
+    block back, three, one or six partners, none -- solves within the
+    backward-error bound, and the partner tables are in use exactly when
+    the options ask for them."""
+    s = config_sequence(1, asym=0.05)
+    S = KKTSolver(s.n, s.indptr, s.indices, fp32=fp32, solve_far_blocks=far_blocks, solve_far_ctas=far_ctas)
+    st = S.stats()
+    if far_blocks < 0 or far_ctas < 0:
+        assert st["solve_far_ctas"] == 0 and st["solve_far_rows"] == 0
+    else:
+        assert st["solve_far_ctas"] >= 1 and st["solve_far_rows"] > 0, st
+        if far_ctas > 0:
+            assert st["solve_far_ctas"] <= far_ctas
+    S.refactor(_t(s.values(29)))
+    _check(S, np.random.default_rng(3).standard_normal(s.n), fp32)
+    # refinement on top of the split solves still reaches the target
+    b = _t(s.csr(29) @ s.x_true(29))
+    x = S.solve(b)
+    info = S.refine(b, x, tol=1e-14, max_it=60)
+    assert info["converged"], info
+
+
+def test_raw_solves_far_sources_smallest_case():
+    """The 200-bus system has a handful of far rows only one block back
+    (solve_far_blocks = 1): the partner path at its smallest."""
+    s = config_sequence(0, asym=0.05)
+    S = KKTSolver(s.n, s.indptr, s.indices, solve_far_blocks=1)
+    assert S.stats()["solve_far_rows"] > 0
+    S.refactor(_t(s.values(9)))
+    _check(S, np.random.default_rng(9).standard_normal(s.n), False)
