@@ -395,12 +395,17 @@ kkt_status kkt_export_scaling(kkt_ctx *ctx, double *out_dev, kkt_stream stream);
 /*
  * Batched same-pattern systems (configuration option max_batch >= B).  All
  * arrays are batch innermost: entry k of system s at k * B + s for values
- * (nnz x B), entry i of system s at i * B + s for vectors (n x B).  One warp
- * works on one row or task for 32 systems, one system per lane, so that every
- * access is coalesced across the batch and each FP64 instruction serves 32
- * systems.  Refinement is classic (Sec. 5.1) and stops when every system
- * reaches tol; omega_host (B doubles, may be NULL) receives each system's
- * scaled residual and *iters the solves used.
+ * (nnz x B), entry i of system s at i * B + s for vectors (n x B).  Work
+ * items are (row or task, system) pairs, claimed in topological order with
+ * every system of a row or task together; one warp runs the single-system
+ * body on one pair, the row's entries across its lanes, so a warp's loads
+ * step through one system's entries B values apart (not coalesced across the
+ * batch: a warp per row of 4 adjacent systems, 8 lanes each, was measured
+ * slower on the 10,000-bus x 64 case).  The B systems' independent
+ * dependency chains run side by side and fill the GPU that one system leaves
+ * idle.  Refinement is classic (Sec. 5.1) and stops when every system reaches
+ * tol; omega_host (B doubles, may be NULL) receives each system's scaled
+ * residual and *iters the solves used.
  */
 kkt_status kkt_batch_refactor(kkt_ctx *ctx, int B, const double *values_dev, kkt_stream stream);
 kkt_status kkt_batch_solve(kkt_ctx *ctx, int B, const double *b_dev, double *x_dev, kkt_stream stream);
