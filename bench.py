@@ -680,6 +680,7 @@ def run_native(args, ws, rank, local):
         "dtype": dname, "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "nnz": nnz, "nnz_lu": st["nnz_lu"],
                    "levels": st["n_levels"], "value_sets": K, "dense_rows": st["dense_rows"],
+                   "solve_partner_ctas": st["solve_far_ctas"], "solve_far_rows": st["solve_far_rows"],
                    "factors": ("FP32, FP64 residual/refinement/pivot test" if wl["fp32"] else "FP64")
                               + (", LDL^T of the symmetric values" if wl.get("symmetric") else ", LU"),
                    "refine": wl["refine"],
