@@ -75,7 +75,9 @@ def test_70000bus_fp32_factors_and_refined_omega():
     S = KKTSolver(s.n, s.indptr, s.indices, fp32=True, refine_mode="auto")
     S.refactor(vt)
     x = S.solve(bt)
-    info = S.refine(bt, x, 1e-14, 20)
+    # budget of 40 solves: with FP32 factors the count moves with the
+    # triangular solves' summation order (7-11 measured at this size)
+    info = S.refine(bt, x, 1e-14, 40)
     assert info["converged"], info
     assert oracle.omega(s.n, s.indptr, s.indices, v, b, x.cpu().numpy()) <= 1e-14
 
@@ -96,8 +98,8 @@ def test_uneven_48_queue_omega_and_transposed():
     Q.solve_transpose(gs, lams)
     for k, q in enumerate(seqs):
         if not (om[k].item() <= 1e-14):
-            sols[k].refine(bs[k], xs[k], 1e-14, 20)
-        sols[k].refine_transpose(gs[k], lams[k], 1e-14, 20)
+            sols[k].refine(bs[k], xs[k], 1e-14, 40)
+        sols[k].refine_transpose(gs[k], lams[k], 1e-14, 40)
         v = q.values(0)
         w = oracle.omega(q.n, q.indptr, q.indices, v, q.rhs(0), xs[k].cpu().numpy())
         assert w <= 1e-14, (k, q.n, w)

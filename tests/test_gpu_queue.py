@@ -39,7 +39,7 @@ def test_queue_refactor_solve_refine_and_replay(fp32):
         for k, s in enumerate(seqs):
             # a system that the fixed in-graph refinement left short finishes on its context
             if om[k].item() > 1e-14:
-                sols[k].refine(bs[k], xs[k], 1e-14, 20)
+                sols[k].refine(bs[k], xs[k], 1e-14, 40)
             v, b = s.values(step), s.rhs(step)
             w = oracle.omega(s.n, s.indptr, s.indices, v, b, xs[k].cpu().numpy())
             assert w <= 1e-14, (k, step, w, om[k].item())
@@ -48,7 +48,7 @@ def test_queue_refactor_solve_refine_and_replay(fp32):
     lams = [torch.zeros_like(g) for g in gs]
     Q.solve_transpose(gs, lams)
     for k, s in enumerate(seqs):
-        sols[k].refine_transpose(gs[k], lams[k], 1e-14, 20)
+        sols[k].refine_transpose(gs[k], lams[k], 1e-14, 40)
         At = s.csr(2).T.tocsr()
         assert oracle.omega(s.n, At.indptr, At.indices, At.data, gs[k].cpu().numpy(),
                             lams[k].cpu().numpy()) <= 1e-14
