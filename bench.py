@@ -516,7 +516,8 @@ def run_native(args, ws, rank, local):
     seq = config_sequence(wl["cfg"])
     n, nnz, K = seq.n, seq.nnz, seq.steps
     S = KKTSolver(n, seq.indptr, seq.indices, fp32=wl["fp32"], refine_mode=wl["refine"],
-                  symmetric=wl.get("symmetric", False), device=local)
+                  symmetric=wl.get("symmetric", False), solve_far_blocks=args.solve_far_blocks,
+                  solve_far_ctas=args.solve_far_ctas, device=local)
     dname = "f32" if wl["fp32"] else "f64"
     rng = np.random.default_rng(1234 + rank)
     vals = [torch.tensor(seq.values(k), device=dev) for k in range(K)]
@@ -964,6 +965,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the batched and FP32 comparisons (about a minute)")
+    ap.add_argument("--solve-far-blocks", type=int, default=0,
+                    help="single-system workloads: the library option solve_far_blocks (0: its default, "
+                         "-1: no partner CTAs)")
+    ap.add_argument("--solve-far-ctas", type=int, default=0,
+                    help="single-system workloads: the library option solve_far_ctas (0: its default)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
