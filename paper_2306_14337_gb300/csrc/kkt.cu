@@ -3247,6 +3247,15 @@ void kkt_destroy(kkt_ctx *c) {
 
 // Analysis of the pattern of A, or of Q A when a row permutation is given by
 // the options or computed from values_host (max-product matching).
+// Option ranges shared by kkt_analyze(_values) and kkt_load_analysis.
+static bool options_valid(const kkt_options &o) {
+    return o.fgmres_restart >= 1 && o.max_refine >= 0 && o.spin_limit >= 1 &&
+           o.refine_mode >= KKT_REFINE_CLASSIC && o.refine_mode <= KKT_REFINE_FGMRES_JACOBI &&
+           o.jacobi_sweeps >= 0 && o.dense_block >= -1 && o.refactor_row_cap >= 0 &&
+           o.refine_auto_ratio >= 0.0 && o.refine_auto_ratio < 1.0 && o.max_batch >= 1 && o.cta_warps >= 0 &&
+           o.refactor_ctas >= 0 && o.solve_ctas >= 0 && o.solve_far_blocks >= -1 && o.solve_far_ctas >= -1;
+}
+
 static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, const double *values_host,
                               const kkt_options *opt, kkt_ctx **out) {
     ApiRange nvtx_range(values_host ? "kkt_analyze_values" : "kkt_analyze");
@@ -3255,13 +3264,7 @@ static kkt_status analyze_ctx(int n, const int *row_ptr, const int *col_idx, con
     std::unique_ptr<kkt_ctx> c(new (std::nothrow) kkt_ctx());
     if (!c) return KKT_ERR_ALLOC;
     if (opt) c->opt = *opt; else kkt_default_options(&c->opt);
-    if (c->opt.fgmres_restart < 1 || c->opt.max_refine < 0 || c->opt.spin_limit < 1 ||
-        c->opt.refine_mode < KKT_REFINE_CLASSIC || c->opt.refine_mode > KKT_REFINE_FGMRES_JACOBI ||
-        c->opt.jacobi_sweeps < 0 || c->opt.dense_block < -1 || c->opt.refactor_row_cap < 0 ||
-        !(c->opt.refine_auto_ratio >= 0.0 && c->opt.refine_auto_ratio < 1.0) ||
-        c->opt.max_batch < 1 || c->opt.cta_warps < 0 || c->opt.refactor_ctas < 0 ||
-        c->opt.solve_ctas < 0 || c->opt.solve_far_blocks < -1 ||
-        c->opt.solve_far_ctas < -1) {
+    if (!options_valid(c->opt)) {
         g_last_error = "invalid option";
         return KKT_ERR_ARG;
     }
@@ -4719,6 +4722,10 @@ kkt_status kkt_load_analysis(const void *buf, size_t size, const kkt_options *op
     std::unique_ptr<kkt_ctx> c(new (std::nothrow) kkt_ctx());
     if (!c) return KKT_ERR_ALLOC;
     if (opt) c->opt = *opt; else kkt_default_options(&c->opt);
+    if (!options_valid(c->opt)) {
+        g_last_error = "invalid option";
+        return KKT_ERR_ARG;
+    }
     Analysis &a = c->an;
     try {
         ImgReader r{b, size - 8};

@@ -166,8 +166,10 @@ class KKTSolver:
     def from_analysis(cls, image: bytes, indptr, indices, **opts):
         """A context from a saved analysis image (kkt_load_analysis) instead of
         a new analysis; indptr/indices are the caller's pattern (kept for the
-        binding's checks), opts as for the constructor (ordering options are
-        fixed by the image)."""
+        binding's checks); opts are kkt_options fields by name (``fp32`` is
+        accepted for ``factor_fp32``, ``refine_mode`` by its name, ``device``
+        as for the constructor).  Ordering options are fixed by the image;
+        an unknown or fixed option raises TypeError."""
         obj = cls.__new__(cls)
         obj._lib = _capi.load()
         obj._rp, obj._ci = _i32(indptr), _i32(indices)
@@ -175,16 +177,21 @@ class KKTSolver:
         obj.nnz = int(obj._ci.size)
         opt = _capi.Options()
         obj._lib.kkt_default_options(C.byref(opt))
+        fields = {name for name, _ in _capi.Options._fields_}
+        fixed = {"ordering", "user_perm", "user_row_perm", "device"}   # set by the image / below
         for k, v in opts.items():
             if k == "device":
                 continue
+            k = {"fp32": "factor_fp32"}.get(k, k)     # the constructor's name for it
+            if k not in fields or k in fixed:
+                raise TypeError(f"from_analysis: unsupported option {k!r}")
             if k == "refine_mode":
                 v = _REFINE[v]
             setattr(opt, k, int(v) if isinstance(v, bool) else v)
         dev = opts.get("device", 0)
         obj.device = None if dev is None else torch.device("cuda", int(dev))
         opt.device = -1 if dev is None else int(dev)
-        obj.fp32 = bool(opts.get("factor_fp32", False))
+        obj.fp32 = bool(opt.factor_fp32)
         obj._perm = obj._row_perm = None
         obj._opt = opt
         h = C.c_void_p()

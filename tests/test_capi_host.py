@@ -297,3 +297,28 @@ def test_far_source_options_validated():
         with pytest.raises(KKTError) as ei:
             KKTSolver(s.n, s.indptr, s.indices, device=None, **kw)
         assert ei.value.status == _capi.KKT_ERR_ARG
+
+
+def test_loaded_analysis_validates_options_like_analyze():
+    """kkt_load_analysis applies the same option ranges as kkt_analyze."""
+    s = config_sequence(0)
+    img = KKTSolver(s.n, s.indptr, s.indices, device=None).save_analysis()
+    ok = KKTSolver.from_analysis(img, s.indptr, s.indices, device=None, solve_far_blocks=-1)
+    assert ok.stats()["n"] == s.n
+    for kw in (dict(solve_far_blocks=-2), dict(solve_far_ctas=-3), dict(fgmres_restart=0),
+               dict(max_batch=0), dict(refine_auto_ratio=1.5), dict(dense_block=-2)):
+        with pytest.raises(KKTError) as ei:
+            KKTSolver.from_analysis(img, s.indptr, s.indices, device=None, **kw)
+        assert ei.value.status == _capi.KKT_ERR_ARG, kw
+
+
+def test_from_analysis_option_names():
+    """from_analysis takes the constructor's fp32 for factor_fp32 and refuses
+    names it cannot honour instead of ignoring them."""
+    s = config_sequence(0)
+    img = KKTSolver(s.n, s.indptr, s.indices, device=None).save_analysis()
+    B = KKTSolver.from_analysis(img, s.indptr, s.indices, device=None, fp32=True, refine_mode="fgmres")
+    assert B.fp32 and B.stats()["factor_fp32"] == 1
+    for kw in (dict(fp23=True), dict(ordering=1)):
+        with pytest.raises(TypeError):
+            KKTSolver.from_analysis(img, s.indptr, s.indices, device=None, **kw)
