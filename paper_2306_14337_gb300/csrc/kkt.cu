@@ -3006,6 +3006,28 @@ static kkt_status upload(kkt_ctx *c) {
                 }
             }
         }
+        // The waits of the partner CTAs end only if every far range lies
+        // among the early sources (at least one whole block back) and each
+        // task's far rows are listed in step order; check both before any
+        // kernel relies on them.
+        {
+            bool ok = true;
+            for (int T : chain) {
+                for (int i = a.task_lo[T]; ok && i <= a.task_hi[T]; i++) {
+                    if (cf_f[i] != ce_f[i]) ok = ce_f[i] < cf_f[i] && cf_f[i] <= csl[i];
+                    if (ok && cf_b[i] != ce_b[i]) ok = csl[n + (size_t)i] <= cf_b[i] && cf_b[i] < ce_b[i];
+                }
+            }
+            for (size_t q = 0; ok && q + 4 <= part_f.size(); q += 4) {
+                const int o0 = part_f[q], cnt = part_f[q + 1], b0 = part_b[q], cntb = part_b[q + 1];
+                for (int r = 1; ok && r < cnt; r++) ok = fr_f2[o0 + r - 1] < fr_f2[o0 + r];
+                for (int r = 1; ok && r < cntb; r++) ok = fr_b2[b0 + r - 1] > fr_b2[b0 + r];
+            }
+            if (!ok) {
+                g_last_error = "internal: inconsistent far-source plan of the triangular solves";
+                return KKT_ERR_ARG;
+            }
+        }
         int *d = nullptr;
         const size_t words = 3 * (size_t)nt + 3 * (size_t)(nt + xr_f.size() + xr_b.size()) + chain.size() +
                              4 * (size_t)n + blk0.size() + binfo.size() + pack_rows.size() + 2 * (size_t)n +
